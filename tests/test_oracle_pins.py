@@ -1,0 +1,364 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the paper's
+worked example (Sec. 2, Fig. 1), exhaustive search (frustration index by
+definition, max-cut for all-negative graphs, Sec. 1), Harary's theorem
+(Sec. 2), the fundamental-cycle rule of the graphB+ algorithm (appendix),
+library routines (scipy BFS distances, components, CSR; numpy matrix powers)
+and closed forms (graphL's quadratic loss, Eq. 3-4).
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.csgraph as csg
+
+import synth
+from tests._bruteforce import exact_frustration, max_cut
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _fig1():
+    edges, meta = [], {}
+    for line in open(os.path.join(GOLDEN, "paper_fig1.txt")):
+        line = line.split("#")[0].split()
+        if not line:
+            continue
+        if line[0] == "edge":
+            edges.append((int(line[1]), int(line[2])))
+        else:
+            meta[line[0]] = int(line[1])
+    return meta, np.array(edges, np.int32)
+
+
+# ------------------------------------------------------------ hash primitives
+
+def test_splitmix64_published_first_output(oracle):
+    # SplitMix64 from state 0: the first output is the finaliser applied to the
+    # golden-ratio increment; its published value is 0xE220A8397B1DCDAF.
+    assert oracle.mix64(0x9E3779B97F4A7C15) == 0xE220A8397B1DCDAF
+
+
+def test_hash_primitives_are_bijective_on_samples(oracle):
+    xs = np.random.Generator(np.random.PCG64(5)).integers(0, 2**63, 20000, dtype=np.uint64)
+    assert len({oracle.mix64(int(x)) for x in xs}) == len(set(int(x) for x in xs))
+    assert len({oracle.fmix32(i) for i in range(20000)}) == 20000
+    assert oracle.fmix32(0) == 0
+
+
+def test_state_hash_is_a_subset_sum(oracle):
+    rng = np.random.Generator(np.random.PCG64(9))
+    n = 300
+    a = (rng.random(n) < 0.3).astype(np.uint8)
+    b = ((rng.random(n) < 0.3) & (a == 0)).astype(np.uint8)
+    ha, hb, hab = oracle.state_hash(a), oracle.state_hash(b), oracle.state_hash(a | b)
+    assert (ha + hb) % (1 << 64) == hab
+    assert oracle.state_hash(np.zeros(n, np.uint8)) == 0
+
+
+# ------------------------------------------------------------------ ingest
+
+def test_clean_graph_matches_scipy_components_and_csr(oracle):
+    rng = np.random.Generator(np.random.PCG64(3))
+    n = 60
+    a = rng.integers(0, n, 70)
+    b = rng.integers(0, n, 70)
+    keep = a != b
+    a, b = a[keep], b[keep]
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    key = np.unique(lo * n + hi)
+    lo, hi = key // n, key % n
+    sign = np.where(rng.random(lo.shape[0]) < 0.4, -1, 1).astype(np.int8)
+    g = oracle.clean_graph(n, lo, hi, sign)
+    A = sp.coo_matrix((np.ones(lo.shape[0]), (lo, hi)), shape=(n, n))
+    ncomp, lab = csg.connected_components(A, directed=False)
+    sizes = np.bincount(lab)
+    best = max(range(ncomp), key=lambda c: (sizes[c], -np.min(np.nonzero(lab == c)[0])))
+    members = np.nonzero(lab == best)[0]
+    assert g.n == members.shape[0]
+    assert np.array_equal(np.nonzero(g.vmap >= 0)[0], members)
+    assert np.array_equal(g.vmap[members], np.arange(g.n))
+    # CSR against scipy's symmetric adjacency (sorted rows)
+    S = sp.coo_matrix((np.ones(g.m), (g.eu, g.ev)), shape=(g.n, g.n))
+    S = (S + S.T).tocsr()
+    S.sort_indices()
+    assert np.array_equal(g.rowptr, S.indptr)
+    assert np.array_equal(g.col, S.indices)
+    assert np.all(g.eu < g.ev)
+    keys = g.eu.astype(np.int64) * g.n + g.ev
+    assert np.all(np.diff(keys) > 0)
+
+
+def test_clean_graph_errors(oracle):
+    O = oracle
+    with pytest.raises(O.OracleError) as e:
+        O.clean_graph(3, [0, 1], [1, 1], [1, 1])
+    assert e.value.code == -4  # self-loop
+    with pytest.raises(O.OracleError) as e:
+        O.clean_graph(3, [0, 1], [1, 2], [1, 0])
+    assert e.value.code == -5  # invalid sign
+    with pytest.raises(O.OracleError) as e:
+        O.clean_graph(3, [0, 1], [1, 3], [1, 1])
+    assert e.value.code == -9  # out of range
+    with pytest.raises(O.OracleError) as e:
+        O.clean_graph(3, [0, 1, 1], [1, 2, 0], [1, 1, -1])
+    assert e.value.code == -6  # same pair, both signs
+    with pytest.raises(O.OracleError) as e:
+        O.clean_graph(3, [0, 1, 1], [1, 2, 0], [1, 1, 1], flags=O.LOAD_LCC)
+    assert e.value.code == -7  # duplicate without merge
+    g = O.clean_graph(3, [0, 1, 1], [1, 2, 0], [1, 1, 1])
+    assert g.m == 2
+    with pytest.raises(O.OracleError) as e:
+        O.clean_graph(4, [0, 2], [1, 3], [1, 1], flags=O.LOAD_MERGE_DUP)
+    assert e.value.code == -8  # disconnected without LCC
+    g = O.clean_graph(4, [0, 2], [1, 3], [1, 1])
+    assert g.n == 2 and list(g.vmap) == [0, 1, -1, -1]  # tie -> smallest id
+
+
+# ------------------------------------------------------------ trees, labels
+
+def _tree_checks(O, g, seed, t):
+    root, parent, clab, level = O.tree(g, seed, t)
+    A = sp.coo_matrix((np.ones(g.m), (g.eu, g.ev)), shape=(g.n, g.n))
+    dist = csg.shortest_path(A, directed=False, unweighted=True, indices=root)
+    assert np.array_equal(level, dist.astype(np.int32)), "levels are BFS distances"
+    assert root == O.tree_root(seed, t, g.n)
+    nb = {}
+    for j in range(g.n):
+        nb[j] = {int(c): int(s) for c, s in zip(g.col[g.rowptr[j]:g.rowptr[j + 1]],
+                                                 g.colneg[g.rowptr[j]:g.rowptr[j + 1]])}
+    tree_edges = 0
+    for v in range(g.n):
+        if v == root:
+            assert parent[v] == -1
+            continue
+        p = int(parent[v])
+        assert p in nb[v] and level[p] == level[v] - 1
+        cands = [u for u in nb[v] if level[u] == level[v] - 1]
+        assert p == min(cands, key=lambda u: O.parent_key(seed, t, u, v))
+        tree_edges += 1
+        # every tree edge is satisfied by the state
+        assert clab[v] ^ clab[p] ^ nb[v][p] == 0
+    assert tree_edges == g.n - 1
+    # labels = parity of negative edges on the root path, vertex 0 canonical
+    par_lab = np.zeros(g.n, np.uint8)
+    for v in range(g.n):
+        x, s = v, 0
+        while x != root:
+            s ^= nb[x][int(parent[x])]
+            x = int(parent[x])
+        par_lab[v] = s
+    assert np.array_equal(clab, par_lab ^ par_lab[0])
+    assert clab[0] == 0
+    # graphB+ (appendix): S = number of non-tree edges with a negative
+    # fundamental cycle, computed by walking both endpoints up to their LCA
+    tree_set = {(min(v, int(parent[v])), max(v, int(parent[v]))) for v in range(g.n) if v != root}
+    neg_cycles = 0
+    for a, b, s in zip(g.eu, g.ev, g.eneg):
+        if (int(a), int(b)) in tree_set:
+            continue
+        x, y, prod = int(a), int(b), int(s)
+        while x != y:
+            if level[x] >= level[y]:
+                prod ^= nb[x][int(parent[x])]
+                x = int(parent[x])
+            else:
+                prod ^= nb[y][int(parent[y])]
+                y = int(parent[y])
+        neg_cycles += prod
+    assert g.m - len(tree_set) == g.m - g.n + 1  # Corollary, Sec. 2
+    S = O.frustration(g, clab)
+    assert S == neg_cycles
+    return S, clab
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_trees_labels_counts_on_random_graphs(oracle, case):
+    n, u, v, s = synth.random_connected(9 + 3 * case, 6 + 4 * case, seed=100 + case)
+    g = oracle.clean_graph(n, u, v, s)
+    fr, _ = exact_frustration(g.n, g.eu, g.ev, g.eneg)
+    for t in range(12):
+        S, _ = _tree_checks(oracle, g, seed=case, t=t)
+        assert S >= fr
+
+
+def test_paper_example_all_sign_patterns(oracle):
+    meta, E = _fig1()
+    n = meta["vertices"]
+    balanced_patterns = 0
+    for pat in range(32):
+        sign = np.array([-1 if (pat >> i) & 1 else 1 for i in range(5)], np.int8)
+        g = oracle.clean_graph(n, E[:, 0], E[:, 1], sign)
+        fr, nbal = exact_frustration(g.n, g.eu, g.ev, g.eneg)
+        assert fr <= meta["max_frustration"]
+        res = oracle.sample(g, seed=0, t0=0, K=32)
+        cl = oracle.cloud(res["labels"], res["counts"])
+        assert np.all(res["counts"] >= fr)
+        if fr == 0:
+            balanced_patterns += 1
+            assert nbal == 1  # the unique bipartition, up to the global flip
+            assert np.all(res["counts"] == 0)
+            assert cl["S"].shape[0] == 1 and cl["count"][0] == 32
+        else:
+            assert res["counts"].min() == fr
+    assert balanced_patterns == meta["balanced_patterns"]
+
+
+@pytest.mark.parametrize("case", range(5))
+def test_harary_planted_balance(oracle, case):
+    n, u, v, s, side = synth.planted_balanced(10 + 2 * case, 10 + 3 * case, seed=200 + case)
+    g = oracle.clean_graph(n, u, v, s)
+    res = oracle.sample(g, seed=case, t0=0, K=24)
+    assert np.all(res["counts"] == 0)
+    cl = oracle.cloud(res["labels"], res["counts"])
+    assert cl["S"].shape[0] == 1
+    want = (side ^ side[0]).astype(np.uint8)
+    assert np.array_equal(res["labels"][0], want)
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_all_negative_maxcut(oracle, case):
+    n, u, v, _ = synth.random_connected(8 + 2 * case, 8 + 2 * case, seed=300 + case)
+    neg = -np.ones(u.shape[0], np.int8)
+    g = oracle.clean_graph(n, u, v, neg)
+    fr, _ = exact_frustration(g.n, g.eu, g.ev, g.eneg)
+    assert fr == g.m - max_cut(g.n, g.eu, g.ev)  # Sec. 1: max-cut equivalence
+    res = oracle.sample(g, seed=1, t0=0, K=16)
+    assert np.all(res["counts"] >= fr)
+
+
+def test_all_negative_bipartite_gives_zero(oracle):
+    # even cycle + chords between the two colour classes: bipartite
+    n = 10
+    u = list(range(n))
+    v = [(i + 1) % n for i in range(n)]
+    u += [0, 2, 1]
+    v += [3, 7, 4]
+    neg = -np.ones(len(u), np.int8)
+    g = oracle.clean_graph(n, u, v, neg)
+    assert g.m - max_cut(g.n, g.eu, g.ev) == 0
+    res = oracle.sample(g, seed=3, t0=0, K=20)
+    assert np.all(res["counts"] == 0)
+
+
+def test_parent_choice_is_randomized(oracle):
+    # 4-cycle: the vertex opposite the root always has two candidate parents;
+    # over many trees each candidate should win about half the time
+    g = oracle.clean_graph(4, [0, 1, 2, 3], [1, 2, 3, 0], [1, 1, 1, 1])
+    wins, total = 0, 0
+    roots = np.zeros(4, int)
+    for t in range(2000):
+        root, parent, _, _ = oracle.tree(g, 11, t)
+        roots[root] += 1
+        opp = (root + 2) % 4
+        wins += int(parent[opp] == min((opp + 1) % 4, (opp + 3) % 4))
+        total += 1
+    assert abs(wins / total - 0.5) < 0.05
+    assert np.all(np.abs(roots / 2000 - 0.25) < 0.05)
+
+
+# ------------------------------------------------------------------ cloud
+
+def test_cloud_invariants_and_sharding(oracle):
+    n, u, v, s = synth.random_connected(14, 10, seed=41)
+    g = oracle.clean_graph(n, u, v, s)
+    K = 64
+    res = oracle.sample(g, seed=2, t0=0, K=K)
+    cl = oracle.cloud(res["labels"], res["counts"])
+    assert cl["count"].sum() == K
+    assert np.all(np.diff(cl["first_tree"]) > 0)
+    for f, S, H in zip(cl["first_tree"], cl["S"], cl["H"]):
+        assert S == oracle.frustration(g, res["labels"][f])
+        assert H == oracle.state_hash(res["labels"][f])
+    # distinct states
+    reps = res["labels"][cl["first_tree"]]
+    assert len({r.tobytes() for r in reps}) == reps.shape[0]
+    # sharding: the halves, merged by state, give the whole
+    a = oracle.sample(g, seed=2, t0=0, K=K // 2)
+    b = oracle.sample(g, seed=2, t0=K // 2, K=K // 2)
+    assert np.array_equal(np.concatenate([a["labels"], b["labels"]]), res["labels"])
+    ca = oracle.cloud(a["labels"], a["counts"], t0=0)
+    cb = oracle.cloud(b["labels"], b["counts"], t0=K // 2)
+    merged = {}
+    for c, lab in ((ca, a["labels"]), (cb, b["labels"])):
+        for i in range(c["S"].shape[0]):
+            key = lab[c["first_tree"][i] - (0 if c is ca else K // 2)].tobytes()
+            f, cnt = merged.get(key, (1 << 60, 0))
+            merged[key] = (min(f, int(c["first_tree"][i])), cnt + int(c["count"][i]))
+    whole = {res["labels"][f].tobytes(): (int(f), int(c)) for f, c in zip(cl["first_tree"], cl["count"])}
+    assert merged == whole
+
+
+# ------------------------------------------------------------------ graphL
+
+def _small_graph(oracle, seed=5):
+    n, u, v, s = synth.random_connected(12, 14, seed=seed)
+    return oracle.clean_graph(n, u, v, s)
+
+
+def test_graphl_gradient_central_differences(oracle):
+    g = _small_graph(oracle)
+    R = 3
+    gam = synth.gamma0(g.n, R, seed=1).astype(np.float64)
+    grad = oracle.graphl_grad_f64(g, gam)
+    h = 1e-3
+    for v in range(g.n):
+        for r in range(R):
+            gp = gam.copy(); gp[v, r] += h
+            gm = gam.copy(); gm[v, r] -= h
+            Lp, _ = oracle.graphl_loss_f64(g, gp)
+            Lm, _ = oracle.graphl_loss_f64(g, gm)
+            fd = (Lp[r] - Lm[r]) / (2 * h)  # exact for a function linear in gam[v, r]
+            assert abs(fd - grad[v, r]) <= 1e-9 * (1 + abs(grad[v, r]))
+
+
+def test_graphl_loss_closed_forms(oracle):
+    g = _small_graph(oracle, seed=6)
+    rng = np.random.Generator(np.random.PCG64(2))
+    theta = np.where(rng.random((g.n, 4)) < 0.5, -1.0, 1.0)
+    L, F = oracle.graphl_loss_f64(g, theta)
+    assert np.array_equal(L, F.astype(np.float64))  # Eq. 3 at theta in {+-1} is Eq. 2
+    Fr, flip = oracle.graphl_round_f32(g, theta.astype(np.float32), want_flip=True)
+    assert np.array_equal(Fr, F)
+    assert np.array_equal(flip.sum(axis=1), F)
+    fr, _ = exact_frustration(g.n, g.eu, g.ev, g.eneg)
+    assert np.all(F >= fr)
+    # zero state: every edge contributes 1/2
+    L0, _ = oracle.graphl_loss_f64(g, np.zeros((g.n, 2)))
+    assert np.all(L0 == g.m / 2)
+    # the loss equals m/2 - 1/2 G^T A_sigma G / 2 with A_sigma the signed adjacency
+    A = np.zeros((g.n, g.n))
+    for a, b, s in zip(g.eu, g.ev, g.eneg):
+        A[a, b] = A[b, a] = -1.0 if s else 1.0
+    gam = synth.gamma0(g.n, 2, seed=4).astype(np.float64)
+    L, _ = oracle.graphl_loss_f64(g, gam)
+    want = g.m / 2 - 0.25 * np.einsum("ir,ij,jr->r", gam, A, gam)
+    assert np.allclose(L, want, rtol=1e-12, atol=1e-12)
+
+
+def test_graphl_descent_is_a_matrix_power(oracle):
+    g = _small_graph(oracle, seed=7)
+    A = np.zeros((g.n, g.n))
+    for a, b, s in zip(g.eu, g.ev, g.eneg):
+        A[a, b] = A[b, a] = -1.0 if s else 1.0
+    alpha, steps = 0.05, 40
+    gam0 = synth.gamma0(g.n, 3, seed=8).astype(np.float64)
+    out, exps, _ = oracle.graphl_descent_f64(g, gam0, alpha, steps, renorm_log2=0)
+    want = np.linalg.matrix_power(np.eye(g.n) + 0.5 * alpha * A, steps) @ gam0
+    assert np.allclose(out, want, rtol=1e-10, atol=1e-12)
+    assert np.all(exps == 0)
+
+
+def test_graphl_renorm_keeps_signs(oracle):
+    g = _small_graph(oracle, seed=9)
+    gam0 = synth.gamma0(g.n, 4, seed=10)
+    a, ea, _ = oracle.graphl_descent_f64(g, gam0, 0.9, 60, renorm_log2=0)
+    b, eb, _ = oracle.graphl_descent_f64(g, gam0, 0.9, 60, renorm_log2=8)
+    assert np.all(eb > 0)
+    assert np.array_equal(np.sign(a), np.sign(b))
+    assert np.array_equal(a, b * np.exp2(eb.astype(np.float64))[None, :])  # exact powers of two
+    c, ec = oracle.graphl_descent_f32(g, gam0, 0.9, 60, renorm_log2=8)
+    d, ed = oracle.graphl_descent_f32(g, gam0, 0.9, 60, renorm_log2=16)
+    assert np.array_equal(np.sign(c), np.sign(d))
