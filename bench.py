@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""graphBpp / graphL benchmark on GB300 (one JSON line on rank 0).
+
+Workload (N=1): the 2^20-vertex R-MAT signed graph (a,b,c,d = 0.57, 0.19,
+0.19, 0.05; 2^24 distinct undirected edges; planted two-faction balance with
+10% iid sign flips; largest connected component), K = 1024 randomized-BFS
+trees per step in one batched launch (16 words of 64 trees).  One step is the
+whole graphBpp hot path on one batch: tree sampling + parity labels + state
+hash (sb_sample_trees), frustration counts (sb_frustration) and cloud
+insertion (sb_cloud).  Ingest is done once, outside the timed region (it is
+timed inside the e2e leg).  Metric: edge-evals/s = trees x |E| / s.
+
+Also reported: the plain path (one tree per launch) on the same GPU, graphL
+steps/s (R = 256 start points on the same graph), the end-to-end number
+through the C ABI with host buffers, the roofline of the dominant kernel and
+the CPU oracle on the host cores.
+
+--impl reference times the CPU oracle (plain C, all host cores through a
+thread pool) on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "graphBpp edge-evals/s (trees x |E| / s), batched"
+UNIT = "edge-evals/s"
+WORKLOAD = "rmat20_2faction_K1024"
+TREES = 1024
+SEED = 0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=20)
+    ap.add_argument("--edges-log2", type=int, default=24)
+    ap.add_argument("--no-extras", action="store_true", help="skip the plain / graphL / e2e / cpu legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args):
+    import synth
+
+    n, u, v, s = synth.rmat_two_faction(scale=args.scale, m_target=1 << args.edges_log2)
+    return n, u, v, s
+
+
+def config_dict(args, n_clean, m_clean, world):
+    return {
+        "workload": WORKLOAD if (args.scale, args.edges_log2) == (20, 24) else f"rmat{args.scale}_e{args.edges_log2}",
+        "graph": f"R-MAT scale {args.scale}, 2^{args.edges_log2} undirected edges, two factions + 10% sign noise, LCC",
+        "n": n_clean,
+        "m": m_clean,
+        "trees_per_step": TREES,
+        "words_per_launch": TREES // 64,
+        "l2": "inputs larger than L2 (CSR 2m x 4 B plus labels and BFS state exceed 129 MB)",
+        "parallelism": f"replicas{world}" if world > 1 else "single-gpu",
+    }
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sms, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sms.append(float(p[1]))
+                mx = max(mx, float(p[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, p[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sms)}
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_graph(n, u, v, s):
+    import oracle as O
+
+    return O.clean_graph(n, u, v, s)
+
+
+def oracle_trees(g, t0, count, cores):
+    """Samples `count` trees with the oracle on `cores` threads; returns seconds."""
+    import oracle as O
+
+    t = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(lambda i: O.sample(g, SEED, t0 + i, 1, want_labels=False), range(count)))
+    return time.perf_counter() - t
+
+
+def cpu_baseline(g, budget_s=12.0):
+    cores = os.cpu_count() or 1
+    done, el = 0, 0.0
+    while el < budget_s:
+        el += oracle_trees(g, 10_000_000 + done, cores, cores)
+        done += cores
+    return {"value": done * g.m / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} trees (BFS tree, labels, count, hash) of the same graph, {cores} threads, {el:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    n, u, v, s = workload(args)
+    g = oracle_graph(n, u, v, s)
+    cores = os.cpu_count() or 1
+    per_step = cores
+    for i in range(args.warmup):
+        oracle_trees(g, i * per_step, per_step, cores)
+    el = 0.0
+    for i in range(args.steps):
+        el += oracle_trees(g, (args.warmup + i) * per_step, per_step, cores)
+    value = args.steps * per_step * g.m / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": config_dict(args, g.n, g.m, 1),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} trees per step ({cores} threads), the same graph"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- ours
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import paper_2311_00869_gb300 as P
+
+    n, u, v, s = workload(args)
+    stream = torch.cuda.current_stream()
+    sb = P.SignedBal(local, stream=stream)
+    n1, m1, _ = sb.load_graph(n, u, v, s)
+    steps_total = args.warmup + args.steps
+    sb.cloud_reset(max_states=(steps_total + 2) * TREES + 64)
+    counts = torch.empty(TREES, dtype=torch.int32, device="cuda")
+    hashes = torch.empty(TREES, dtype=torch.int64, device="cuda")
+
+    # trees are independent: rank r takes its own tree ranges (weak scaling)
+    def step(i):
+        t0 = ((i * world) + rank) * TREES
+        sb.sample_trees(SEED, t0, TREES)
+        sb.frustration(counts, hashes)
+        return sb.cloud_insert()
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    sb.profile_read()
+    sb.profile(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    sb.profile(False)
+    prof = sb.profile_read()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * TREES * m1 / (ms_step / 1000.0)
+    launches = sum(c for _, c in prof.values())
+
+    cl, fr_min = sb.cloud()
+    extras = {"fr_min": int(fr_min), "distinct_states": int(cl["S"].shape[0])}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": config_dict(args, n1, m1, world),
+        "gpu_launches": launches, "clocks": clk,
+        "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
+    }
+    line["roofline"] = roofline(prof, args.steps, n1, m1)
+    if not args.no_extras and rank == 0:
+        try:
+            extras.update(plain_leg(sb, m1))
+        except Exception as e:  # a failing side leg must not hide the main number
+            extras["plain_error"] = repr(e)
+        try:
+            extras.update(graphl_leg(P, sb, n1, m1))
+        except Exception as e:
+            extras["graphl_error"] = repr(e)
+        try:
+            line["e2e"] = e2e_leg(P, sb, n, u, v, s)
+        except Exception as e:
+            line["e2e"] = {"error": repr(e)}
+        try:
+            g = oracle_graph(n, u, v, s)
+            line["cpu_baseline"] = cpu_baseline(g)
+        except Exception as e:
+            line["cpu_baseline"] = {"error": repr(e)}
+    line["extras"] = extras
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sb.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def roofline(prof, steps, n, m):
+    """Dominant kernel family with its algorithmic bytes per launch."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    src = "measured" if "hbm_gbs" in peaks else "fallback"
+    fam = max(prof, key=lambda k: prof[k][0])
+    ms, launches = prof[fam]
+    W = TREES // 64
+    # algorithmic bytes per launch (see the design notes for the derivation)
+    per_launch = {
+        # one CSR scan (2m x 4 B), rowptr-free work items (16 B per row),
+        # labels written once (n x W x 8 B) and the frontier of every vertex
+        # read once per word (n x W x 8 B)
+        "bfs": 2 * m * 4 + 16 * n + 2 * n * W * 8,
+        # edge stream (8 B per edge) + every label word read once (n x W x 8 B) + counts
+        "score": 8 * m + n * W * 8 + 4 * TREES,
+        "hash": n * W * 8 + n * 8 + 8 * TREES,
+        "cloud": n * W * 8 + n * W * 8,
+    }.get(fam)
+    if per_launch is None or launches == 0 or ms <= 0:
+        return {"bound": "hbm", "kernel": fam, "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                "traffic": None}
+    avg_s = ms / launches / 1000.0
+    achieved = per_launch / avg_s / 1e9
+    return {"bound": "hbm", "kernel": fam, "achieved": achieved, "peak": hbm, "peak_source": src, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "algorithmic_bytes_per_launch": per_launch,
+            "avg_launch_ms": 1000 * avg_s, "launches": launches}
+
+
+def plain_leg(sb, m):
+    """The same 64 trees, one tree per launch (plain) vs one 64-tree launch."""
+    import torch
+
+    sb.cloud_reset(max_states=8192)
+    t0 = 50_000_000
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for i in range(64):
+        sb.sample_trees(SEED, t0 + i, 1)
+        sb.frustration()
+        sb.cloud_insert()
+    torch.cuda.synchronize()
+    plain = time.perf_counter() - t
+    c_plain, _ = sb.cloud()
+    sb.cloud_reset(max_states=8192)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    sb.sample_trees(SEED, t0, 64)
+    counts, _ = sb.frustration()
+    sb.cloud_insert()
+    torch.cuda.synchronize()
+    batched = time.perf_counter() - t
+    c_b, fr_b = sb.cloud()
+    same = bool(np.array_equal(c_plain["S"], c_b["S"]) and np.array_equal(c_plain["count"], c_b["count"]))
+    return {"plain_edge_evals_per_s": 64 * m / plain, "batched64_edge_evals_per_s": 64 * m / batched,
+            "plain_vs_batched_same_cloud": same, "plain64_fr_min": int(c_plain["S"].min())}
+
+
+def graphl_leg(P, sb, n, m, R=256, steps=50, alpha=0.05):
+    import torch
+
+    import synth
+
+    g0 = torch.from_numpy(synth.gamma0(n, R, seed=0)).cuda()
+    out = torch.empty_like(g0)
+    sb.graphL_descent(g0, alpha, 5, out=out)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sb.profile_read()
+    sb.profile(True)
+    e0.record()
+    _, exps, _, F_final = sb.graphL_descent(g0, alpha, steps, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    sb.profile(False)
+    prof = sb.profile_read()
+    ms = e0.elapsed_time(e1)
+    F0, _ = sb.graphL_round(g0)
+    return {"graphl_steps_per_s": steps / (ms / 1000.0), "graphl_R": R, "graphl_steps": steps,
+            "graphl_init_steps_per_s": R * steps / (ms / 1000.0), "graphl_F_min_start": int(F0.min()),
+            "graphl_F_min_final": int(F_final.min()), "graphl_row_kernel_ms_per_step": prof["gl_rows"][0] / steps}
+
+
+def e2e_leg(P, sb, n, u, v, s, steps=3):
+    """Through the C ABI with host buffers: per step the COO goes host -> device
+    from pinned memory, is ingested, K trees are sampled, and the counts,
+    hashes and cloud come back to host memory."""
+    import torch
+
+    pu = torch.from_numpy(u).pin_memory()
+    pv = torch.from_numpy(v).pin_memory()
+    ps = torch.from_numpy(s).pin_memory()
+    hc = torch.empty(TREES, dtype=torch.int32).pin_memory()
+    hh = torch.empty(TREES, dtype=torch.int64).pin_memory()
+    m1 = 0
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for i in range(steps):
+        _, m1, _ = sb.load_graph(n, pu, pv, ps)
+        sb.sample_trees(SEED, 90_000_000 + i * TREES, TREES)
+        sb.frustration(hc, hh)
+        cl, fr = sb.cloud()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t
+    h2d = u.nbytes + v.nbytes + s.nbytes
+    d2h = hc.numel() * 4 + hh.numel() * 8 + int(cl["S"].shape[0]) * 24
+    return {"value": steps * TREES * m1 / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "includes": "H2D of the COO, ingest, sample, count, cloud, D2H"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

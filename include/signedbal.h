@@ -1,0 +1,229 @@
+/*
+ * signedbal.h -- C ABI of the GB300 (sm_103a) graphBpp / graphL library.
+ *
+ * Method: Shebaro & Tesic, "Scaling Frustration Index and Corresponding
+ * Balanced State Discovery for Real Signed Graphs" (arXiv 2311.00869).
+ *
+ * Conventions for every entry point
+ *   - Pointers are plain host or device pointers; sizes are int64_t.  Unless a
+ *     function says otherwise, array arguments are DEVICE pointers on the
+ *     context's device (a torch tensor's data_ptr() works).  Output arrays
+ *     may instead be host pointers where marked "host or device": the library
+ *     then copies through cudaMemcpyAsync and synchronises the stream.
+ *   - The caller owns every buffer it passes.  The context owns the loaded
+ *     graph, the labels of the last sampled batch, the cloud and its scratch.
+ *   - Work is enqueued on the context's stream.  Calls that return host
+ *     scalars (n_out, m_out, n_states_out, fr_min_out) synchronise it.
+ *   - Errors are returned as negative sb_status codes; no C++ exception
+ *     crosses the ABI.  sb_last_error() gives a one-line reason.  After
+ *     SB_ERR_CUDA the context should be destroyed.
+ *   - One context must not be used from two host threads at once.
+ */
+#ifndef SIGNEDBAL_H
+#define SIGNEDBAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sb_ctx sb_ctx;
+typedef int32_t sb_status;
+
+#define SB_OK 0
+#define SB_ERR_ARG (-1)          /* bad argument or size                              */
+#define SB_ERR_CUDA (-2)         /* CUDA runtime error                                */
+#define SB_ERR_OOM (-3)          /* allocation failed                                 */
+#define SB_ERR_SELF_LOOP (-4)    /* input edge (v, v)                                 */
+#define SB_ERR_BAD_SIGN (-5)     /* sign not +1 / -1                                  */
+#define SB_ERR_INCONSISTENT (-6) /* same vertex pair present with both signs          */
+#define SB_ERR_DUPLICATE (-7)    /* repeated pair and SB_LOAD_MERGE_DUP not set       */
+#define SB_ERR_DISCONNECTED (-8) /* several components and SB_LOAD_LCC not set        */
+#define SB_ERR_RANGE (-9)        /* vertex id outside [0, n)                          */
+#define SB_ERR_STATE (-10)       /* call out of order (no graph, no sampled batch)    */
+#define SB_ERR_CLOUD_FULL (-11)  /* cloud reached its state capacity                  */
+#define SB_ERR_TIMEOUT (-12)     /* a bounded device wait gave up                     */
+#define SB_ERR_DEVICE_CHECK (-13)/* a device-side consistency check failed            */
+
+/* sb_load_graph flags */
+#define SB_LOAD_LCC 1u        /* keep the largest connected component              */
+#define SB_LOAD_MERGE_DUP 2u  /* merge repeated pairs of equal sign                */
+
+/* Device memory hooks: alloc(bytes, stream, user) -> device pointer or NULL;
+   free(ptr, stream, user). */
+typedef void* (*sb_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*sb_free_fn)(void* ptr, void* stream, void* user);
+
+/* One entry of the frustration cloud, Alg. 1 and Eq. 1: a distinct balanced
+   state with its switch count S, its count C, the first tree that produced
+   it, and its 64-bit state hash. */
+typedef struct sb_cloud_entry {
+    uint64_t hash;       /* sum of vertex weights over vertices labelled 1, mod 2^64 */
+    int32_t S;           /* edge signs switched to reach the state (Alg. 1 line 7)   */
+    int32_t count;       /* trees that produced the state (Alg. 1 line 13)           */
+    int64_t first_tree;  /* global index of the first such tree                      */
+} sb_cloud_entry;
+
+/* ---------------------------------------------------------------- context */
+
+/* Creates a context on CUDA device `device`; `cuda_stream` is a cudaStream_t
+   (NULL = the legacy default stream).  *out is NULL on failure. */
+sb_status sb_create(sb_ctx** out, int device, void* cuda_stream);
+void sb_destroy(sb_ctx* ctx);
+const char* sb_status_str(sb_status s);
+const char* sb_last_error(const sb_ctx* ctx);
+/* Replaces cudaMalloc/cudaFree for context-owned buffers (e.g. with a
+   framework's caching allocator).  Call before sb_load_graph. */
+sb_status sb_set_allocator(sb_ctx* ctx, sb_alloc_fn alloc, sb_free_fn free_fn, void* user);
+/* Waits for the stream and reports any pending device error. */
+sb_status sb_sync(sb_ctx* ctx);
+
+/* Kernel families timed by the profiler (sb_profile / sb_profile_read). */
+#define SB_PROF_BFS 0      /* tree sampler + labeller (cooperative BFS)        */
+#define SB_PROF_SCORE 1    /* frustration counts                              */
+#define SB_PROF_HASH 2     /* state hash                                      */
+#define SB_PROF_CLOUD 3    /* cloud insertion and checks                      */
+#define SB_PROF_INGEST 4   /* graph ingest                                    */
+#define SB_PROF_GL_ROWS 5  /* graphL adjoint / descent step over CSR rows     */
+#define SB_PROF_GL_FWD 6   /* graphL edge-parallel loss                       */
+#define SB_PROF_OTHER 7    /* set-up and small kernels                        */
+#define SB_PROF_N 8
+
+/* Enables (1) or disables (0) CUDA-event timing of every kernel launch on the
+   context's stream, by family.  Off by default. */
+sb_status sb_profile(sb_ctx* ctx, int enable);
+/* Waits for the stream, then writes the device time (ms) and number of
+   kernel launches per family since the last read (host arrays of SB_PROF_N
+   entries, nullable), and resets them.  Launch counts are kept even when
+   timing is off. */
+sb_status sb_profile_read(sb_ctx* ctx, double* ms_out, int64_t* launches_out);
+
+/* ------------------------------------------------------------ graph ingest */
+
+/*
+ * Loads an undirected signed graph (Def. "Signed graph", Sec. 2) from a COO
+ * list: edge i joins src[i] and dst[i] with sign[i] in {+1, -1}.  The
+ * appendix "Implementation" paragraph describes the cleaning: self-loops and
+ * invalid signs are errors, a pair with both signs is an inconsistency,
+ * repeated pairs (either orientation) are merged with SB_LOAD_MERGE_DUP,
+ * and with SB_LOAD_LCC the largest connected component is kept (most
+ * vertices; ties go to the component with the smallest vertex id), its
+ * vertices renumbered in increasing original id.  The first offending input
+ * edge decides among range / self-loop / sign errors.
+ * src, dst, sign: host or device, m entries each.  n >= 1, 2*m < 2^31.
+ * Outputs (host pointers): *n_out, *m_out after cleaning.  vmap_out (host or
+ * device, n entries, nullable) receives old id -> new id or -1.
+ * Synchronous.  Replaces any previous graph and clears the cloud.
+ */
+sb_status sb_load_graph(sb_ctx* ctx, int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                        const int8_t* sign, uint32_t flags, int64_t* n_out, int64_t* m_out, int32_t* vmap_out);
+
+/* Exports the cleaned edge list: u < v, lexicographic order, neg = 1 for a
+   negative edge.  Each pointer host or device, m_out entries, nullable. */
+sb_status sb_graph_edges(sb_ctx* ctx, int32_t* u_out, int32_t* v_out, int8_t* neg_out);
+
+/* Exports the CSR (rows sorted ascending): rowptr n+1 entries, col and neg
+   2m entries.  Host or device, nullable. */
+sb_status sb_graph_csr(sb_ctx* ctx, int32_t* rowptr_out, int32_t* col_out, int8_t* neg_out);
+
+/* ---------------------------------------------------------------- graphBpp */
+
+/*
+ * Samples trees [tree_begin, tree_begin + K) and their balanced states
+ * (Alg. 1 lines 2 and 6; appendix graphB+ algorithm).  Tree t is the
+ * randomized BFS tree defined by
+ *     S   = mix64(seed + G),  K_t = mix64(S + (t + 1) G),  G = 0x9E3779B97F4A7C15
+ *     root r_t = ((K_t >> 32) * n) >> 32
+ *     parent of v = argmin over neighbours u one BFS level up of
+ *                   (fmix32((u ^ y_v) + lo32(K_t)) << 32) | u,
+ *     y_v = hi32(mix64(v ^ S ^ 0xD1B54A32D192ED03))
+ * (mix64 = SplitMix64 finaliser, fmix32 = MurmurHash3 finaliser), and its
+ * state labels each vertex with the parity of negative tree edges on its
+ * root path, canonicalised so vertex 0 has label 0.  A tree is a pure
+ * function of (seed, t): splitting a range gives the same trees.
+ * K >= 1 (at most 64 * 64 per call).  parents_out (device, K x n int32,
+ * nullable; -1 at the root) costs extra shared memory: meant for checks on
+ * small graphs.  Replaces the previous batch.
+ */
+sb_status sb_sample_trees(sb_ctx* ctx, uint64_t seed, int64_t tree_begin, int64_t K, int32_t* parents_out);
+
+/* Canonical labels of the last batch, bit-packed vertex-major:
+   labels_out[v * W + w] bit b = label of tree tree_begin + 64 w + b at vertex v,
+   W = ceil(K / 64); bits of trees >= K are 0.  Host or device. */
+sb_status sb_label(sb_ctx* ctx, uint64_t* labels_out);
+
+/* Alg. 1 line 7 for each tree of the last batch: counts_out[i] = number of
+   edges whose sign differs between the graph and the state of tree
+   tree_begin + i (label(u) XOR label(v) XOR neg).  hashes_out[i] = state
+   hash.  Host or device; hashes_out nullable. */
+sb_status sb_frustration(sb_ctx* ctx, int32_t* counts_out, uint64_t* hashes_out);
+
+/*
+ * Inserts the last batch into the context's frustration cloud (Alg. 1 lines
+ * 8-14; the key is the canonical state, checked bit for bit whenever two
+ * trees share a hash) and exports it: entries in order of first appearance.
+ * out: host or device, cap entries; out = NULL with cap = 0 only inserts
+ * and reports.  Host outputs: *n_states_out, *fr_min_out = min S (Eq. 1;
+ * nullable).  Returns SB_ERR_CLOUD_FULL when the cloud's capacity was
+ * reached (entries beyond it are dropped and counted nowhere) or when
+ * 0 < cap < n_states (then only cap entries are written).  The cloud accumulates across batches until
+ * sb_cloud_reset or sb_load_graph.
+ */
+sb_status sb_cloud(sb_ctx* ctx, sb_cloud_entry* out, int64_t cap, int64_t* n_states_out, int32_t* fr_min_out);
+
+/* Empties the cloud; max_states (0 = 4096) sets its capacity in states.
+   hash_bits in [1, 64] (0 = 64) truncates the table key for testing the
+   collision path; exported hashes stay full. */
+sb_status sb_cloud_reset(sb_ctx* ctx, int64_t max_states, int32_t hash_bits);
+
+/* Canonical labels of cloud state `idx` (order of sb_cloud), bit-packed:
+   bits_out[v / 64] bit (v % 64) = label of vertex v.  ceil(n/64) words,
+   host or device. */
+sb_status sb_cloud_state(sb_ctx* ctx, int64_t idx, uint64_t* bits_out);
+
+/* ------------------------------------------------------------------ graphL */
+
+/*
+ * Relaxed loss of Eq. 3 and discrete loss of Eq. 2 (Alg. 2 lines 5-6) for R
+ * starting points at once: gamma is n x R float32 row-major (gamma[v*R + r]).
+ * loss_out[r] = sum over edges (1 - e_uv G_u G_v) / 2, each undirected edge
+ * once; F_out[r] = edges with e_uv theta_u theta_v = -1, theta = +1 iff
+ * G >= 0 (nullable).  Edge-parallel, deterministic.  Device pointers.
+ */
+sb_status sb_graphL_fwd(sb_ctx* ctx, const float* gamma, int32_t R, float* loss_out, int32_t* F_out);
+
+/*
+ * Adjoint of sb_graphL_fwd (Eq. 4): grad_out[v*R + r] =
+ * -1/2 * gout[r] * sum_{j in N(v)} e_vj gamma[j*R + r], summed over CSR rows
+ * in a fixed order (no float atomics; bitwise reproducible).  Device pointers.
+ */
+sb_status sb_graphL_bwd(sb_ctx* ctx, const float* gamma, int32_t R, const float* gout, float* grad_out);
+
+/*
+ * Alg. 2 descent from gamma0 for `steps` updates G <- G - alpha dL/dG (every
+ * start point weighted 1).  After each update a column whose largest |G|
+ * reached 2^renorm_log2 is scaled by 2^-renorm_log2 and exps_out[r] grows by
+ * renorm_log2 (0 disables; powers of two keep every sign and every rounded
+ * value).  gamma_out receives the final G (n x R); exps_out (int32 R);
+ * F_trace (int32 steps x R, nullable) the discrete loss before each update;
+ * F_final (int32 R, nullable) the discrete loss of the final G (Alg. 2 lines
+ * 11-24).  Device pointers; gamma0 and gamma_out may alias.
+ */
+sb_status sb_graphL_descent(sb_ctx* ctx, const float* gamma0, float* gamma_out, int32_t R, float alpha, int32_t steps,
+                            int32_t renorm_log2, int32_t* exps_out, int32_t* F_trace, int32_t* F_final);
+
+/*
+ * Alg. 2 final loop: theta = +1 iff G >= 0, F_out[r] = frustrated edges
+ * (exact integer), flip_out (nullable) bit-packed per start point:
+ * flip_out[r * ceil(m/64) + i/64] bit i%64 = 1 when edge i (order of
+ * sb_graph_edges) must switch sign.  Device pointers.
+ */
+sb_status sb_graphL_round(sb_ctx* ctx, const float* gamma, int32_t R, int32_t* F_out, uint64_t* flip_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIGNEDBAL_H */

@@ -1,0 +1,677 @@
+// sb_bpp.cu -- graphBpp hot path: batched randomized-BFS tree sampling with
+// parity labelling (Alg. 1 line 6 through the appendix graphB+ algorithm,
+// restated with Harary's bipartition, Sec. 2), the state hash that keys the
+// frustration cloud, and the bit-sliced frustration scorer (Alg. 1 line 7).
+//
+// Data layout (vertex-major, 64 trees per uint64 word):
+//   labels[v * W + w]  bit b = parity label of tree 64 w + b at vertex v
+//   vis / frontier     [v * Wb + w] for the Wb words of one BFS launch
+// A BFS launch grows up to 32 words (2048 trees) at once, level by level, in
+// one cooperative persistent kernel: a group of G lanes owns one vertex (lane
+// = word), gathers its neighbours' frontier words with coalesced row loads,
+// and picks each newly reached tree's parent as the argmin of the packed key
+// (fmix32((u ^ y_v) + a_t) << 32 | u).  fmix32 is a bijection, so the hash
+// alone orders the candidates of one (tree, vertex): comparing 32-bit hashes
+// is the 64-bit packed argmin.  Rows longer than SB_BFS_CHUNK are split over
+// several groups that merge with 64-bit atomicMin on the packed key.
+#include <algorithm>
+
+#include "sb_internal.cuh"
+
+#define BFS_THREADS 256
+#define BFS_THREADS_PAR 128
+#define SYNC_WORDS 16
+#define BAR_LIMIT_CYCLES (4ll * 1000 * 1000 * 1000)  // ~2 s at 2 GHz
+
+struct BfsArgs {
+    const sb_bfs_item* items;
+    int64_t n_items;
+    const int32_t* col;
+    const int32_t* hub_vertex;
+    int64_t n_hubs;
+    uint64_t* lab;   // n x Wt
+    int Wt, w0, Wb;
+    uint64_t* vis;   // n x Wb
+    uint64_t* fr0;
+    uint64_t* fr1;
+    int32_t* done;
+    uint64_t* hubnew;   // n_hubs x Wb
+    uint64_t* hubbest;  // n_hubs x Wb x 64
+    uint32_t* sync;
+    int32_t* parents;   // K x n or null
+    int64_t n;
+    uint64_t S;         // seed key
+    int64_t tree0;      // global index of batch tree 0
+};
+
+// ----------------------------------------------------------- grid barrier
+// Cooperative launch makes every block resident; the wait is still bounded
+// and reports a timeout through sync[6] instead of hanging.
+__device__ __forceinline__ void grid_barrier(uint32_t* sync, unsigned nblocks)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile uint32_t* gen = sync + 5;
+        uint32_t g = *gen;
+        __threadfence();
+        uint32_t arrived = atomicAdd(sync + 4, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(sync + 4, 0u);
+            __threadfence();
+            atomicAdd(sync + 5, 1u);
+        } else {
+            long long t0 = clock64();
+            while (*gen == g) {
+                __nanosleep(40);
+                if (clock64() - t0 > BAR_LIMIT_CYCLES) {
+                    atomicOr(sync + 6, 1u);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ unsigned group_mask(int G)
+{
+    if (G >= 32) return 0xffffffffu;
+    unsigned base = (threadIdx.x & 31u) & ~(unsigned)(G - 1);
+    return ((1u << G) - 1u) << base;
+}
+
+template <int G, bool PAR>
+__global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
+    k_bfs(BfsArgs A)
+{
+    constexpr int BD = PAR ? BFS_THREADS_PAR : BFS_THREADS;
+    extern __shared__ uint32_t smem[];
+    uint32_t* akey = smem;                 // Wb * 64 tree salts
+    uint32_t* best = smem + SB_WORDS_MAX * 64;  // 64 x BD running minima
+    int32_t* bestu = (int32_t*)(best + 64 * BD);  // 64 x BD winners (PAR only)
+    __shared__ uint32_t s_any;
+
+    const int tid = threadIdx.x;
+    const int gl = tid & (G - 1);
+    const bool act = gl < A.Wb;
+    const unsigned gmask = group_mask(G);
+    const int64_t groups_total = (int64_t)gridDim.x * (BD / G);
+    const int64_t group_id = (int64_t)blockIdx.x * (BD / G) + tid / G;
+    const unsigned nblocks = gridDim.x;
+
+    for (int i = tid; i < A.Wb * 64; i += BD) akey[i] = (uint32_t)sb_tree_key(A.S, A.tree0 + 64 * (int64_t)A.w0 + i);
+    if (tid == 0) s_any = 0;
+    __syncthreads();
+
+    const int Wb = A.Wb, Wt = A.Wt, w0 = A.w0;
+    int L = 1;
+    while (true) {
+        const uint64_t* __restrict__ cur = (L & 1) ? A.fr0 : A.fr1;
+        uint64_t* __restrict__ nxt = (L & 1) ? A.fr1 : A.fr0;
+        bool any_new = false;
+
+        // ---- phase A: every work item (whole rows, and chunks of split rows)
+        for (int64_t it = group_id; it < A.n_items; it += groups_total) {
+            const sb_bfs_item itm = A.items[it];
+            const int32_t v = itm.v;
+            const int32_t d = A.done[v];
+            if (d >= 0 && L >= d + 3) continue;
+            const uint64_t vis_w = act ? A.vis[(int64_t)v * Wb + gl] : ~0ull;
+            const uint64_t U = ~vis_w;
+            const int32_t* cp = A.col + itm.beg;
+            const int len = itm.end - itm.beg;
+            if (itm.hub >= 0) {
+                // chunk of a split row: candidates merge through global atomics
+                if (U) {
+                    const uint32_t y = sb_child_salt(A.S, (uint32_t)v);
+                    uint64_t acc = 0;
+                    uint64_t* hb = A.hubbest + ((int64_t)itm.hub * Wb + gl) * 64;
+                    for (int j = 0; j < len; j++) {
+                        const uint32_t c = (uint32_t)cp[j];
+                        const uint32_t u = c & SB_ID_MASK;
+                        uint64_t f = cur[(int64_t)u * Wb + gl] & U;
+                        if (f) {
+                            acc |= f;
+                            const uint64_t lu = A.lab[(int64_t)u * Wt + w0 + gl] ^ ((c >> 31) ? ~0ull : 0ull);
+                            const uint32_t hx = u ^ y;
+                            while (f) {
+                                const int t = __ffsll((long long)f) - 1;
+                                f &= f - 1;
+                                const uint32_t h = sb_fmix32(hx + akey[gl * 64 + t]);
+                                const unsigned long long key =
+                                    ((unsigned long long)h << 32) | ((unsigned long long)u << 1) | ((lu >> t) & 1ull);
+                                atomicMin((unsigned long long*)(hb + t), key);
+                            }
+                        }
+                    }
+                    if (acc) atomicOr((unsigned long long*)(A.hubnew + (int64_t)itm.hub * Wb + gl), acc);
+                }
+                continue;
+            }
+            uint64_t once = 0, twice = 0, labx = 0;
+            if (U) {
+#pragma unroll 4
+                for (int j = 0; j < len; j++) {
+                    const uint32_t c = (uint32_t)cp[j];
+                    const uint32_t u = c & SB_ID_MASK;
+                    const uint64_t f = cur[(int64_t)u * Wb + gl] & U;
+                    if (f) {
+                        const uint64_t lu = A.lab[(int64_t)u * Wt + w0 + gl] ^ ((c >> 31) ? ~0ull : 0ull);
+                        twice |= once & f;
+                        once |= f;
+                        labx |= f & lu;
+                    }
+                }
+            }
+            // trees reached through two or more candidates need the hashed argmin
+            const uint64_t multi = PAR ? once : twice;
+            if (multi) {
+                const uint32_t y = sb_child_salt(A.S, (uint32_t)v);
+                uint64_t labm = 0, seen = 0;
+                for (int j = 0; j < len; j++) {
+                    const uint32_t c = (uint32_t)cp[j];
+                    const uint32_t u = c & SB_ID_MASK;
+                    uint64_t f = cur[(int64_t)u * Wb + gl] & multi;
+                    if (f) {
+                        const uint64_t lu = A.lab[(int64_t)u * Wt + w0 + gl] ^ ((c >> 31) ? ~0ull : 0ull);
+                        const uint32_t hx = u ^ y;
+                        while (f) {
+                            const int t = __ffsll((long long)f) - 1;
+                            f &= f - 1;
+                            const uint32_t h = sb_fmix32(hx + akey[gl * 64 + t]);
+                            if (!((seen >> t) & 1ull) || h < best[t * BD + tid]) {
+                                seen |= 1ull << t;
+                                best[t * BD + tid] = h;
+                                labm = (labm & ~(1ull << t)) | (((lu >> t) & 1ull) << t);
+                                if (PAR) bestu[t * BD + tid] = (int32_t)u;
+                            }
+                        }
+                    }
+                }
+                labx = (labx & ~multi) | (labm & multi);
+                if (PAR && A.parents) {
+                    for (uint64_t b = once; b;) {
+                        const int t = __ffsll((long long)b) - 1;
+                        b &= b - 1;
+                        A.parents[(64 * (int64_t)(w0 + gl) + t) * A.n + v] = bestu[t * BD + tid];
+                    }
+                }
+            }
+            if (act) {
+                if (once) {
+                    A.lab[(int64_t)v * Wt + w0 + gl] |= labx & once;
+                    A.vis[(int64_t)v * Wb + gl] = vis_w | once;
+                    any_new = true;
+                }
+                nxt[(int64_t)v * Wb + gl] = once;
+            }
+            if (d < 0) {
+                const bool full = (vis_w | once) == ~0ull;
+                const bool all = __all_sync(gmask, full);
+                if (all && gl == 0) A.done[v] = L;
+            }
+        }
+
+        // ---- phase B: resolve split rows
+        if (A.n_hubs > 0) {
+            grid_barrier(A.sync, nblocks);
+            for (int64_t h = group_id; h < A.n_hubs; h += groups_total) {
+                const int32_t v = A.hub_vertex[h];
+                const int32_t d = A.done[v];
+                if (d >= 0 && L >= d + 3) continue;
+                uint64_t nw = 0, vis_w = ~0ull;
+                if (act) {
+                    vis_w = A.vis[(int64_t)v * Wb + gl];
+                    uint64_t* hn = A.hubnew + h * Wb + gl;
+                    nw = *hn & ~vis_w;
+                    *hn = 0;
+                    uint64_t labx = 0;
+                    uint64_t* hb = A.hubbest + (h * Wb + gl) * 64;
+                    for (uint64_t b = nw; b;) {
+                        const int t = __ffsll((long long)b) - 1;
+                        b &= b - 1;
+                        const uint64_t key = hb[t];
+                        hb[t] = ~0ull;
+                        labx |= (key & 1ull) << t;
+                        if (PAR && A.parents)
+                            A.parents[(64 * (int64_t)(w0 + gl) + t) * A.n + v] = (int32_t)((key >> 1) & SB_ID_MASK);
+                    }
+                    if (nw) {
+                        A.lab[(int64_t)v * Wt + w0 + gl] |= labx;
+                        A.vis[(int64_t)v * Wb + gl] = vis_w | nw;
+                        any_new = true;
+                    }
+                    nxt[(int64_t)v * Wb + gl] = nw;
+                }
+                if (d < 0) {
+                    const bool all = __all_sync(gmask, (vis_w | nw) == ~0ull);
+                    if (all && gl == 0) A.done[v] = L;
+                }
+            }
+        }
+
+        // ---- end of level: any tree grew?
+        if (any_new) s_any = 1;
+        __syncthreads();
+        if (tid == 0) {
+            if (s_any) atomicOr(A.sync + (L % 3), 1u);
+            s_any = 0;
+            if (blockIdx.x == 0) A.sync[(L + 1) % 3] = 0;
+        }
+        grid_barrier(A.sync, nblocks);
+        const uint32_t grew = *(volatile uint32_t*)(A.sync + (L % 3));
+        const uint32_t err = *(volatile uint32_t*)(A.sync + 6);
+        if (!grew || err) break;
+        if (++L > A.n + 1) {
+            if (tid == 0 && blockIdx.x == 0) atomicOr(A.sync + 6, 2u);
+            break;
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && blockIdx.x == 0) A.sync[7] = (uint32_t)L;
+}
+
+// ------------------------------------------------------------ BFS set-up
+__global__ void k_bfs_init(int64_t n, int Wb, int Wt, int w0, int64_t K, uint64_t* vis, uint64_t* fr0, uint64_t* fr1,
+                           uint64_t* lab, int32_t* done)
+{
+    int64_t total = n * Wb;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t v = i / Wb;
+        int w = (int)(i - v * Wb);
+        int64_t trees = K - 64 * (int64_t)(w0 + w);  // trees of this word
+        uint64_t active = trees >= 64 ? ~0ull : ((1ull << trees) - 1ull);
+        vis[i] = ~active;
+        fr0[i] = 0;
+        fr1[i] = 0;
+        lab[v * Wt + w0 + w] = 0;
+        if (w == 0) done[v] = -1;
+    }
+}
+
+__global__ void k_hub_init(int64_t nh, int Wb, uint64_t* hubnew, uint64_t* hubbest)
+{
+    int64_t total = nh * Wb * 64;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        hubbest[i] = ~0ull;
+        if (i < nh * Wb) hubnew[i] = 0;
+    }
+}
+
+__global__ void k_bfs_roots(int64_t n, int Wb, int w0, int64_t K, uint64_t S, int64_t tree0, uint64_t* vis,
+                            uint64_t* fr0, int32_t* parents)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // tree within this launch
+    int64_t tb = 64 * (int64_t)w0 + i;                          // tree within the batch
+    if (i >= 64 * (int64_t)Wb || tb >= K) return;
+    uint64_t key = sb_tree_key(S, tree0 + tb);
+    uint32_t r = sb_root(key, n);
+    int w = (int)(i >> 6);
+    unsigned long long bit = 1ull << (i & 63);
+    atomicOr((unsigned long long*)(vis + (int64_t)r * Wb + w), bit);
+    atomicOr((unsigned long long*)(fr0 + (int64_t)r * Wb + w), bit);
+    if (parents) parents[tb * n + r] = -1;
+}
+
+__global__ void k_flip(const uint64_t* lab, int W, uint64_t* flipw)
+{
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < W) flipw[w] = lab[w];  // row of vertex 0
+}
+
+// H_t = sum of weights of vertices whose canonical label is 1 (mod 2^64).
+// Block: 64 lanes per word bit x 4 vertex strides; grid.y = word.
+#define HASH_VCHUNK 2048
+__global__ void __launch_bounds__(256) k_state_hash(const uint64_t* __restrict__ lab, int64_t n, int W,
+                                                    const uint64_t* __restrict__ flipw,
+                                                    const uint64_t* __restrict__ weight,
+                                                    unsigned long long* __restrict__ H)
+{
+    __shared__ uint64_t part[256];
+    const int w = blockIdx.y;
+    const int b = threadIdx.x & 63, sub = threadIdx.x >> 6;
+    const uint64_t fl = flipw[w];
+    const int64_t v0 = (int64_t)blockIdx.x * HASH_VCHUNK;
+    const int64_t v1 = min(n, v0 + HASH_VCHUNK);
+    uint64_t acc = 0;
+    for (int64_t v = v0 + sub; v < v1; v += 4) {
+        const uint64_t x = lab[v * W + w] ^ fl;
+        const uint64_t wt = weight[v];
+        acc += ((x >> b) & 1ull) ? wt : 0ull;
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    if (sub == 0) {
+        acc = part[b] + part[b + 64] + part[b + 128] + part[b + 192];
+        if (acc) atomicAdd(H + 64 * w + b, (unsigned long long)acc);
+    }
+}
+
+__global__ void k_canon_out(const uint64_t* __restrict__ lab, int64_t total, int W, int64_t K,
+                            const uint64_t* __restrict__ flipw, uint64_t* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int w = (int)(i % W);
+        int64_t trees = K - 64 * (int64_t)w;
+        uint64_t active = trees >= 64 ? ~0ull : ((1ull << trees) - 1ull);
+        out[i] = (lab[i] ^ flipw[w]) & active;
+    }
+}
+
+// ------------------------------------------------------------------ scorer
+// S_t = sum over edges of bit t of lab[u] ^ lab[v] ^ neg.  Each thread owns
+// one word of a batch of <= 32 words and accumulates 64 vertical counters with
+// carry-save adders (ones, twos, fours) plus ripple planes for the eights.
+#define SC_THREADS 256
+#define SC_PLANES 20
+
+__device__ __forceinline__ void csa(uint64_t& h, uint64_t& l, uint64_t a, uint64_t b, uint64_t c)
+{
+    const uint64_t u = a ^ b;
+    h = (a & b) | (u & c);
+    l = u ^ c;
+}
+
+template <int G>
+__global__ void __launch_bounds__(SC_THREADS) k_score(const int2* __restrict__ edges, int64_t m,
+                                                      const uint64_t* __restrict__ lab, int Wt, int w0, int Wb,
+                                                      uint32_t* __restrict__ counts)
+{
+    __shared__ uint32_t scnt[SB_WORDS_MAX * 64];
+    constexpr int NG = SC_THREADS / G;
+    const int tid = threadIdx.x;
+    const int gl = tid & (G - 1), grp = tid / G;
+    const bool act = gl < Wb;
+    for (int i = tid; i < Wb * 64; i += SC_THREADS) scnt[i] = 0;
+    __syncthreads();
+    const int64_t per = sb_cdiv(m, (int64_t)gridDim.x);
+    const int64_t e0 = (int64_t)blockIdx.x * per;
+    const int64_t e1 = min(m, e0 + per);
+    uint64_t ones = 0, twos = 0, fours = 0;
+    uint64_t P[SC_PLANES];
+#pragma unroll
+    for (int b = 0; b < SC_PLANES; b++) P[b] = 0;
+    const uint64_t* __restrict__ lw = lab + w0 + gl;
+    if (act) {
+        for (int64_t e = e0 + grp; e < e1; e += 8 * NG) {
+            uint64_t x[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int64_t ee = e + (int64_t)k * NG;
+                x[k] = 0;
+                if (ee < e1) {
+                    const int2 ed = edges[ee];
+                    const uint32_t vv = (uint32_t)ed.y & SB_ID_MASK;
+                    const uint64_t negm = ed.y < 0 ? ~0ull : 0ull;
+                    x[k] = lw[(int64_t)ed.x * Wt] ^ lw[(int64_t)vv * Wt] ^ negm;
+                }
+            }
+            uint64_t twosA, twosB, foursA, foursB, eights;
+            csa(twosA, ones, ones, x[0], x[1]);
+            csa(twosB, ones, ones, x[2], x[3]);
+            csa(foursA, twos, twos, twosA, twosB);
+            csa(twosA, ones, ones, x[4], x[5]);
+            csa(twosB, ones, ones, x[6], x[7]);
+            csa(foursB, twos, twos, twosA, twosB);
+            csa(eights, fours, fours, foursA, foursB);
+            uint64_t cy = eights;
+#pragma unroll
+            for (int b = 0; b < SC_PLANES; b++) {
+                const uint64_t t = P[b] & cy;
+                P[b] ^= cy;
+                cy = t;
+            }
+        }
+        // each thread saw at most m / 8 groups of eights: < 2^SC_PLANES for m < 2^23 per block range
+#pragma unroll 1
+        for (int t = 0; t < 64; t++) {
+            uint32_t hi = 0;
+#pragma unroll
+            for (int b = 0; b < SC_PLANES; b++) hi |= (uint32_t)((P[b] >> t) & 1ull) << b;
+            const uint32_t val = 8u * hi + 4u * (uint32_t)((fours >> t) & 1ull) + 2u * (uint32_t)((twos >> t) & 1ull) +
+                                 (uint32_t)((ones >> t) & 1ull);
+            if (val) atomicAdd(&scnt[gl * 64 + t], val);
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < Wb * 64; i += SC_THREADS)
+        if (scnt[i]) atomicAdd(counts + 64 * w0 + i, scnt[i]);
+}
+
+// --------------------------------------------------------------- host side
+static int group_for(int Wb)
+{
+    int g = 1;
+    while (g < Wb) g <<= 1;
+    return g;
+}
+
+template <bool PAR>
+static const void* bfs_kernel(int G)
+{
+    switch (G) {
+    case 1: return (const void*)k_bfs<1, PAR>;
+    case 2: return (const void*)k_bfs<2, PAR>;
+    case 4: return (const void*)k_bfs<4, PAR>;
+    case 8: return (const void*)k_bfs<8, PAR>;
+    case 16: return (const void*)k_bfs<16, PAR>;
+    default: return (const void*)k_bfs<32, PAR>;
+    }
+}
+
+static const void* score_kernel(int G)
+{
+    switch (G) {
+    case 1: return (const void*)k_score<1>;
+    case 2: return (const void*)k_score<2>;
+    case 4: return (const void*)k_score<4>;
+    case 8: return (const void*)k_score<8>;
+    case 16: return (const void*)k_score<16>;
+    default: return (const void*)k_score<32>;
+    }
+}
+
+static sb_status ensure_sync(sb_ctx* c)
+{
+    if (!c->sync) {
+        c->sync = (uint32_t*)sb_dalloc(c, sizeof(uint32_t) * SYNC_WORDS);
+        if (!c->sync) return sb_fail(c, SB_ERR_OOM, "sync words");
+    }
+    return SB_OK;
+}
+
+static sb_status run_bfs(sb_ctx* c, int w0, int Wb, int32_t* parents)
+{
+    const bool par = parents != nullptr;
+    const int G = group_for(Wb);
+    const int BD = par ? BFS_THREADS_PAR : BFS_THREADS;
+    const void* fn = par ? bfs_kernel<true>(G) : bfs_kernel<false>(G);
+    size_t smem = sizeof(uint32_t) * (SB_WORDS_MAX * 64 + 64 * BD) + (par ? sizeof(int32_t) * 64 * BD : 0);
+    SB_CHECK_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SB_CHECK_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BD, smem));
+    if (per_sm < 1) return sb_fail(c, SB_ERR_CUDA, "BFS kernel does not fit on an SM");
+    unsigned nblocks = (unsigned)(per_sm * c->num_sms);
+    const int64_t n = c->n;
+    unsigned g = (unsigned)std::min<int64_t>(sb_cdiv(n * Wb, 256), (int64_t)c->num_sms * 16);
+    k_bfs_init<<<g, 256, 0, c->stream>>>(n, Wb, c->W, w0, c->K, c->vis, c->fr0, c->fr1, c->labels, c->done);
+    SB_TRY(sb_after_launch(c, "k_bfs_init"));
+    if (c->n_hubs > 0) {
+        unsigned gh = (unsigned)std::min<int64_t>(sb_cdiv(c->n_hubs * Wb * 64, 256), (int64_t)c->num_sms * 16);
+        k_hub_init<<<gh, 256, 0, c->stream>>>(c->n_hubs, Wb, c->hubnew, c->hubbest);
+        SB_TRY(sb_after_launch(c, "k_hub_init"));
+    }
+    k_bfs_roots<<<(unsigned)sb_cdiv(64 * Wb, 256), 256, 0, c->stream>>>(n, Wb, w0, c->K, sb_seed_key(c->seed),
+                                                                        c->tree_begin, c->vis, c->fr0, parents);
+    SB_TRY(sb_after_launch(c, "k_bfs_roots"));
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync, 0, sizeof(uint32_t) * SYNC_WORDS, c->stream));
+    BfsArgs A;
+    A.items = c->items;
+    A.n_items = c->n_items;
+    A.col = c->col;
+    A.hub_vertex = c->hub_vertex;
+    A.n_hubs = c->n_hubs;
+    A.lab = c->labels;
+    A.Wt = c->W;
+    A.w0 = w0;
+    A.Wb = Wb;
+    A.vis = c->vis;
+    A.fr0 = c->fr0;
+    A.fr1 = c->fr1;
+    A.done = c->done;
+    A.hubnew = c->hubnew;
+    A.hubbest = c->hubbest;
+    A.sync = c->sync;
+    A.parents = parents;
+    A.n = n;
+    A.S = sb_seed_key(c->seed);
+    A.tree0 = c->tree_begin;
+    void* args[] = {&A};
+    SbProf prof(c, SB_PROF_BFS);
+    SB_CHECK_CUDA(c, cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(BD), args, smem, c->stream));
+    return sb_after_launch(c, "k_bfs");
+}
+
+static sb_status check_sync_error(sb_ctx* c)
+{
+    uint32_t err = 0;
+    SB_CHECK_CUDA(c, cudaMemcpyAsync(&err, c->sync + 6, sizeof(err), cudaMemcpyDeviceToHost, c->stream));
+    SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (err & 1u) return sb_fail(c, SB_ERR_TIMEOUT, "BFS grid barrier timed out");
+    if (err & 2u) return sb_fail(c, SB_ERR_DEVICE_CHECK, "BFS exceeded n levels");
+    return SB_OK;
+}
+
+extern "C" sb_status sb_sample_trees(sb_ctx* c, uint64_t seed, int64_t tree_begin, int64_t K, int32_t* parents_out)
+{
+    if (!c) return SB_ERR_ARG;
+    if (!c->has_graph) return sb_fail(c, SB_ERR_STATE, "no graph loaded");
+    if (K < 1 || K > SB_TREES_MAX || tree_begin < 0)
+        return sb_fail(c, SB_ERR_ARG, "K must be in [1, %d] and tree_begin >= 0", SB_TREES_MAX);
+    if (parents_out && !sb_is_device_ptr(parents_out))
+        return sb_fail(c, SB_ERR_ARG, "parents_out must be a device pointer");
+    SB_CHECK_CUDA(c, cudaSetDevice(c->device));
+    SB_TRY(ensure_sync(c));
+    const int64_t n = c->n;
+    const int W = (int)sb_cdiv(K, 64);
+    const int Wb_max = W < SB_WORDS_MAX ? W : SB_WORDS_MAX;
+    // batch storage
+    size_t lab_bytes = sizeof(uint64_t) * (size_t)n * W;
+    if (c->labels_cap < lab_bytes) {
+        sb_dfree(c, c->labels);
+        c->labels = (uint64_t*)sb_dalloc(c, lab_bytes);
+        c->labels_cap = c->labels ? lab_bytes : 0;
+    }
+    sb_dfree(c, c->flipw);
+    sb_dfree(c, c->hashes);
+    sb_dfree(c, c->counts);
+    c->flipw = (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * W);
+    c->hashes = (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * 64 * W);
+    c->counts = (int32_t*)sb_dalloc(c, sizeof(int32_t) * 64 * W);
+    size_t words = (size_t)n * Wb_max;
+    if (c->bfs_cap_words < words) {
+        sb_dfree(c, c->vis);
+        sb_dfree(c, c->fr0);
+        sb_dfree(c, c->fr1);
+        sb_dfree(c, c->hubnew);
+        sb_dfree(c, c->hubbest);
+        c->vis = (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * words);
+        c->fr0 = (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * words);
+        c->fr1 = (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * words);
+        c->hubnew = (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * (size_t)(c->n_hubs > 0 ? c->n_hubs : 1) * Wb_max);
+        c->hubbest =
+            (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * (size_t)(c->n_hubs > 0 ? c->n_hubs : 1) * Wb_max * 64);
+        c->bfs_cap_words = (c->vis && c->fr0 && c->fr1 && c->hubnew && c->hubbest) ? words : 0;
+    }
+    if (!c->done) c->done = (int32_t*)sb_dalloc(c, sizeof(int32_t) * (size_t)n);
+    if (!c->labels || !c->flipw || !c->hashes || !c->counts || !c->bfs_cap_words || !c->done) {
+        c->has_batch = false;
+        return sb_fail(c, SB_ERR_OOM, "BFS batch storage (n=%lld, K=%lld)", (long long)n, (long long)K);
+    }
+    c->seed = seed;
+    c->tree_begin = tree_begin;
+    c->K = K;
+    c->W = W;
+    c->has_batch = false;
+    c->counts_valid = false;
+    c->batch_in_cloud = false;
+    for (int w0 = 0; w0 < W; w0 += SB_WORDS_MAX) {
+        int Wb = W - w0 < SB_WORDS_MAX ? W - w0 : SB_WORDS_MAX;
+        SB_TRY(run_bfs(c, w0, Wb, parents_out));
+    }
+    k_flip<<<1, 64, 0, c->stream>>>(c->labels, W, c->flipw);
+    SB_TRY(sb_after_launch(c, "k_flip"));
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->hashes, 0, sizeof(uint64_t) * 64 * W, c->stream));
+    {
+        SbProf prof(c, SB_PROF_HASH);
+        dim3 hg((unsigned)sb_cdiv(n, HASH_VCHUNK), (unsigned)W);
+        k_state_hash<<<hg, 256, 0, c->stream>>>(c->labels, n, W, c->flipw, c->vweight,
+                                                (unsigned long long*)c->hashes);
+        SB_TRY(sb_after_launch(c, "k_state_hash"));
+    }
+    c->has_batch = true;
+    return SB_OK;
+}
+
+// counts of the current batch (into c->counts), one pass per <= 32 words
+sb_status sb_score_batch(sb_ctx* c)
+{
+    if (c->counts_valid) return SB_OK;
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 64 * c->W, c->stream));
+    if (c->m > 0) {
+        for (int w0 = 0; w0 < c->W; w0 += SB_WORDS_MAX) {
+            int Wb = c->W - w0 < SB_WORDS_MAX ? c->W - w0 : SB_WORDS_MAX;
+            int G = group_for(Wb);
+            const void* fn = score_kernel(G);
+            int per_sm = 0;
+            SB_CHECK_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SC_THREADS, 0));
+            int64_t blocks = (int64_t)c->num_sms * (per_sm > 0 ? per_sm : 1);
+            // every thread must see fewer than 8 * 2^SC_PLANES edges
+            int64_t min_blocks = sb_cdiv(c->m, (int64_t)(SC_THREADS / G) * 8 * ((1 << SC_PLANES) - 1));
+            if (blocks < min_blocks) blocks = min_blocks;
+            const int2* e = c->edges;
+            int64_t m = c->m;
+            const uint64_t* lab = c->labels;
+            int Wt = c->W;
+            uint32_t* cnt = (uint32_t*)c->counts;
+            void* args[] = {(void*)&e, &m, (void*)&lab, &Wt, &w0, &Wb, &cnt};
+            SbProf prof(c, SB_PROF_SCORE);
+            SB_CHECK_CUDA(c, cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(SC_THREADS), args, 0, c->stream));
+            SB_TRY(sb_after_launch(c, "k_score"));
+        }
+    }
+    c->counts_valid = true;
+    return SB_OK;
+}
+
+extern "C" sb_status sb_frustration(sb_ctx* c, int32_t* counts_out, uint64_t* hashes_out)
+{
+    if (!c) return SB_ERR_ARG;
+    if (!c->has_batch) return sb_fail(c, SB_ERR_STATE, "no sampled batch");
+    SB_CHECK_CUDA(c, cudaSetDevice(c->device));
+    SB_TRY(check_sync_error(c));
+    SB_TRY(sb_score_batch(c));
+    if (counts_out) SB_TRY(sb_copy_out(c, counts_out, c->counts, sizeof(int32_t) * c->K));
+    if (hashes_out) SB_TRY(sb_copy_out(c, hashes_out, c->hashes, sizeof(uint64_t) * c->K));
+    return SB_OK;
+}
+
+extern "C" sb_status sb_label(sb_ctx* c, uint64_t* labels_out)
+{
+    if (!c || !labels_out) return SB_ERR_ARG;
+    if (!c->has_batch) return sb_fail(c, SB_ERR_STATE, "no sampled batch");
+    SB_CHECK_CUDA(c, cudaSetDevice(c->device));
+    SB_TRY(check_sync_error(c));
+    int64_t total = c->n * c->W;
+    size_t bytes = sizeof(uint64_t) * (size_t)total;
+    uint64_t* tmp = (uint64_t*)sb_dalloc(c, bytes);
+    if (!tmp) return sb_fail(c, SB_ERR_OOM, "label export");
+    unsigned g = (unsigned)std::min<int64_t>(sb_cdiv(total, 256), (int64_t)c->num_sms * 16);
+    k_canon_out<<<g, 256, 0, c->stream>>>(c->labels, total, c->W, c->K, c->flipw, tmp);
+    sb_status st = sb_after_launch(c, "k_canon_out");
+    if (st == SB_OK) st = sb_copy_out(c, labels_out, tmp, bytes);
+    cudaStreamSynchronize(c->stream);
+    sb_dfree(c, tmp);
+    return st;
+}

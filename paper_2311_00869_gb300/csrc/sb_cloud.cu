@@ -1,0 +1,363 @@
+// sb_cloud.cu -- the frustration cloud (Alg. 1 lines 8-14, Eq. 1): distinct
+// balanced states with their count C and switch count S.
+//
+// The paper keys its std::map by the state's edge-sign string.  Here a state
+// is its canonical vertex labelling (vertex 0 on the +1 side), which for a
+// connected graph is in bijection with that string; the table is keyed by a
+// 64-bit subset-sum hash of the labelling and every hash match is checked bit
+// for bit against the stored state, so a hash collision never merges two
+// states.  Stored states (the matrix B of the scalable variant) live in HBM
+// chunk-major: bits[chunk][state], 64 vertices per word.
+#include <algorithm>
+#include <vector>
+
+#include "sb_internal.cuh"
+
+#define CL_DEFAULT_STATES 4096
+
+__host__ __device__ __forceinline__ uint64_t cl_slot_of(uint64_t key, int64_t slots)
+{
+    return (key ^ (key >> 29) ^ (key >> 47)) & (uint64_t)(slots - 1);
+}
+
+__host__ __device__ __forceinline__ uint64_t cl_key(uint64_t h, int bits)
+{
+    return bits >= 64 ? h : (h & ((1ull << bits) - 1ull));
+}
+
+// Sequential insertion in tree order (first appearance decides the state
+// index).  One thread: the batch holds at most 4096 trees.
+__global__ void k_cloud_assign(const uint64_t* __restrict__ hashes, const int32_t* __restrict__ counts, int64_t K,
+                               int64_t tree_begin, int hash_bits, sb_cloud_slot* table, int64_t slots,
+                               sb_cloud_entry* entries, int64_t max_states, int32_t* meta, int32_t* assign,
+                               int32_t* rep, int32_t* mismatch)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int32_t ns = meta[0];
+    for (int64_t i = 0; i < K; i++) {
+        const uint64_t h = hashes[i];
+        const uint64_t key = cl_key(h, hash_bits);
+        uint64_t s = cl_slot_of(key, slots);
+        int32_t found = -1;
+        int64_t probes = 0;
+        while (table[s].state >= 0 && probes < slots) {
+            if (table[s].key == key) {
+                found = table[s].state;
+                break;
+            }
+            s = (s + 1) & (uint64_t)(slots - 1);
+            probes++;
+        }
+        mismatch[i] = 0;
+        if (found >= 0) {
+            entries[found].count += 1;
+            assign[i] = found;
+            if (entries[found].S != counts[i]) mismatch[i] = 1;  // certainly another state
+        } else if (ns >= max_states || probes >= slots) {
+            meta[1] += 1;
+            assign[i] = -1;
+        } else {
+            table[s].key = key;
+            table[s].state = ns;
+            sb_cloud_entry e;
+            e.hash = h;
+            e.S = counts[i];
+            e.count = 1;
+            e.first_tree = tree_begin + i;
+            entries[ns] = e;
+            rep[ns] = (int32_t)i;
+            assign[i] = ns;
+            ns++;
+        }
+    }
+    meta[0] = ns;
+}
+
+// Canonical label bit of batch tree i at vertex v.
+__device__ __forceinline__ uint32_t cl_bit(const uint64_t* row, const uint64_t* flipw, int64_t i)
+{
+    const int w = (int)(i >> 6), b = (int)(i & 63);
+    return (uint32_t)(((row[w] ^ flipw[w]) >> b) & 1ull);
+}
+
+// One block per 64-vertex chunk.  For each tree of the batch: store the state
+// (trees that created a state in this batch), or compare with the state it
+// was matched to (its creator's labels, or the stored bits of an older state).
+#define CLV_THREADS 256
+__global__ void __launch_bounds__(CLV_THREADS)
+    k_cloud_verify(const uint64_t* __restrict__ lab, int64_t n, int W, const uint64_t* __restrict__ flipw, int64_t K,
+                   const int32_t* __restrict__ assign, const int32_t* __restrict__ rep, uint64_t* bits,
+                   int64_t max_states, int32_t* mismatch)
+{
+    extern __shared__ uint64_t rows[];  // 64 x W
+    const int64_t chunk = blockIdx.x;
+    const int64_t v0 = chunk * 64;
+    const int nv = (int)min((int64_t)64, n - v0);
+    for (int i = threadIdx.x; i < 64 * W; i += CLV_THREADS) {
+        const int r = i / W, w = i - r * W;
+        rows[i] = r < nv ? lab[(v0 + r) * W + w] : 0;
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < K; i += CLV_THREADS) {
+        const int32_t s = assign[i];
+        if (s < 0) continue;
+        uint64_t col = 0;
+        for (int r = 0; r < nv; r++) col |= (uint64_t)cl_bit(rows + r * W, flipw, i) << r;
+        const int32_t creator = rep[s];
+        uint64_t* slot = bits + chunk * max_states + s;
+        if (creator == (int32_t)i) {
+            *slot = col;
+        } else {
+            uint64_t other = 0;
+            if (creator >= 0) {
+                for (int r = 0; r < nv; r++) other |= (uint64_t)cl_bit(rows + r * W, flipw, creator) << r;
+            } else {
+                other = *slot;
+            }
+            if (other != col) mismatch[i] = 1;
+        }
+    }
+}
+
+// Exact comparison (mode 0) or storage (mode 1) of one tree against one state.
+__global__ void k_cloud_pair(const uint64_t* __restrict__ lab, int64_t n, int W, const uint64_t* __restrict__ flipw,
+                             int64_t tree, int32_t state, uint64_t* bits, int64_t max_states, int mode, int32_t* differ)
+{
+    const int64_t nchunks = sb_cdiv(n, 64);
+    for (int64_t chunk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; chunk < nchunks;
+         chunk += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v0 = chunk * 64;
+        const int nv = (int)min((int64_t)64, n - v0);
+        uint64_t col = 0;
+        for (int r = 0; r < nv; r++) col |= (uint64_t)cl_bit(lab + (v0 + r) * W, flipw, tree) << r;
+        uint64_t* slot = bits + chunk * max_states + state;
+        if (mode == 1) *slot = col;
+        else if (*slot != col) atomicOr(differ, 1);
+    }
+}
+
+__global__ void k_cloud_count(const int32_t* __restrict__ mismatch, int64_t K, int32_t* meta)
+{
+    int32_t c = 0;
+    for (int64_t i = threadIdx.x; i < K; i += blockDim.x) c += mismatch[i];
+    for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+    __shared__ int32_t part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t t = 0;
+        for (unsigned i = 0; i < blockDim.x / 32; i++) t += part[i];
+        meta[2] = t;
+    }
+}
+
+__global__ void k_cloud_gather(const uint64_t* __restrict__ bits, int64_t nchunks, int64_t max_states, int64_t s,
+                               uint64_t* out)
+{
+    for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < nchunks; ch += (int64_t)gridDim.x * blockDim.x)
+        out[ch] = bits[ch * max_states + s];
+}
+
+sb_status sb_cloud_alloc(sb_ctx* c)
+{
+    if (c->cl_table) return SB_OK;
+    if (c->cl_max <= 0) c->cl_max = CL_DEFAULT_STATES;
+    if (c->cl_hash_bits <= 0 || c->cl_hash_bits > 64) c->cl_hash_bits = 64;
+    int64_t slots = 1;
+    while (slots < 2 * c->cl_max) slots <<= 1;
+    c->cl_slots = slots;
+    const int64_t nchunks = sb_cdiv(c->n, 64);
+    c->cl_table = (sb_cloud_slot*)sb_dalloc(c, sizeof(sb_cloud_slot) * (size_t)slots);
+    c->cl_entries = (sb_cloud_entry*)sb_dalloc(c, sizeof(sb_cloud_entry) * (size_t)c->cl_max);
+    c->cl_bits = (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * (size_t)nchunks * (size_t)c->cl_max);
+    c->cl_meta = (int32_t*)sb_dalloc(c, sizeof(int32_t) * 8);
+    c->cl_assign = (int32_t*)sb_dalloc(c, sizeof(int32_t) * SB_TREES_MAX);
+    c->cl_rep = (int32_t*)sb_dalloc(c, sizeof(int32_t) * (size_t)c->cl_max);
+    c->cl_mismatch = (int32_t*)sb_dalloc(c, sizeof(int32_t) * SB_TREES_MAX);
+    if (!c->cl_table || !c->cl_entries || !c->cl_bits || !c->cl_meta || !c->cl_assign || !c->cl_rep ||
+        !c->cl_mismatch) {
+        sb_release_cloud(c);
+        return sb_fail(c, SB_ERR_OOM, "cloud storage (%lld states)", (long long)c->cl_max);
+    }
+    // empty slots: state = -1 (all bytes 0xFF)
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->cl_table, 0xFF, sizeof(sb_cloud_slot) * (size_t)slots, c->stream));
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->cl_meta, 0, sizeof(int32_t) * 8, c->stream));
+    c->cl_n_host = 0;
+    return SB_OK;
+}
+
+// Rare path: trees whose hash matched a different state.  Each is re-probed
+// on the host with an exact device comparison against every state sharing
+// its key, and gets a new state when none is equal.
+static sb_status cloud_resolve_collisions(sb_ctx* c)
+{
+    const int64_t K = c->K;
+    std::vector<int32_t> assign(K), mism(K);
+    std::vector<sb_cloud_slot> table(c->cl_slots);
+    int32_t meta[8];
+    SB_CHECK_CUDA(c, cudaMemcpyAsync(assign.data(), c->cl_assign, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, c->stream));
+    SB_CHECK_CUDA(c, cudaMemcpyAsync(mism.data(), c->cl_mismatch, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, c->stream));
+    SB_CHECK_CUDA(c, cudaMemcpyAsync(table.data(), c->cl_table, sizeof(sb_cloud_slot) * c->cl_slots,
+                                     cudaMemcpyDeviceToHost, c->stream));
+    SB_CHECK_CUDA(c, cudaMemcpyAsync(meta, c->cl_meta, sizeof(meta), cudaMemcpyDeviceToHost, c->stream));
+    SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+    std::vector<sb_cloud_entry> entries(meta[0] + K);
+    SB_CHECK_CUDA(c, cudaMemcpy(entries.data(), c->cl_entries, sizeof(sb_cloud_entry) * meta[0], cudaMemcpyDeviceToHost));
+    std::vector<uint64_t> hashes(K);
+    std::vector<int32_t> counts(K);
+    SB_CHECK_CUDA(c, cudaMemcpy(hashes.data(), c->hashes, sizeof(uint64_t) * K, cudaMemcpyDeviceToHost));
+    SB_CHECK_CUDA(c, cudaMemcpy(counts.data(), c->counts, sizeof(int32_t) * K, cudaMemcpyDeviceToHost));
+    int32_t* differ = c->cl_meta + 4;
+    int32_t ns = meta[0];
+    const int64_t nchunks = sb_cdiv(c->n, 64);
+    unsigned g = (unsigned)std::min<int64_t>(sb_cdiv(nchunks, 256), (int64_t)c->num_sms * 8);
+    for (int64_t i = 0; i < K; i++) {
+        if (!mism[i]) continue;
+        entries[assign[i]].count -= 1;
+        const uint64_t key = cl_key(hashes[i], c->cl_hash_bits);
+        uint64_t s = cl_slot_of(key, c->cl_slots);
+        int32_t found = -1;
+        int64_t probes = 0;
+        while (table[s].state >= 0 && probes < c->cl_slots) {
+            if (table[s].key == key) {
+                int32_t st = table[s].state;
+                if (entries[st].S == counts[i]) {
+                    int32_t h_differ = 0;
+                    SB_CHECK_CUDA(c, cudaMemsetAsync(differ, 0, sizeof(int32_t), c->stream));
+                    k_cloud_pair<<<g, 256, 0, c->stream>>>(c->labels, c->n, c->W, c->flipw, i, st, c->cl_bits,
+                                                          c->cl_max, 0, differ);
+                    SB_TRY(sb_after_launch(c, "k_cloud_pair"));
+                    SB_CHECK_CUDA(c, cudaMemcpyAsync(&h_differ, differ, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                                     c->stream));
+                    SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+                    if (!h_differ) {
+                        found = st;
+                        break;
+                    }
+                }
+            }
+            s = (s + 1) & (uint64_t)(c->cl_slots - 1);
+            probes++;
+        }
+        if (found >= 0) {
+            entries[found].count += 1;
+        } else if (ns >= c->cl_max || probes >= c->cl_slots) {
+            meta[1] += 1;
+        } else {
+            table[s].key = key;
+            table[s].state = ns;
+            entries[ns].hash = hashes[i];
+            entries[ns].S = counts[i];
+            entries[ns].count = 1;
+            entries[ns].first_tree = c->tree_begin + i;
+            k_cloud_pair<<<g, 256, 0, c->stream>>>(c->labels, c->n, c->W, c->flipw, i, ns, c->cl_bits, c->cl_max, 1,
+                                                  differ);
+            SB_TRY(sb_after_launch(c, "k_cloud_pair"));
+            ns++;
+        }
+    }
+    meta[0] = ns;
+    SB_CHECK_CUDA(c, cudaMemcpyAsync(c->cl_table, table.data(), sizeof(sb_cloud_slot) * c->cl_slots,
+                                     cudaMemcpyHostToDevice, c->stream));
+    SB_CHECK_CUDA(c, cudaMemcpyAsync(c->cl_entries, entries.data(), sizeof(sb_cloud_entry) * ns, cudaMemcpyHostToDevice,
+                                     c->stream));
+    meta[2] = 0;
+    SB_CHECK_CUDA(c, cudaMemcpyAsync(c->cl_meta, meta, sizeof(int32_t) * 4, cudaMemcpyHostToDevice, c->stream));
+    SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+    return SB_OK;
+}
+
+sb_status sb_cloud_insert_batch(sb_ctx* c)
+{
+    if (c->batch_in_cloud) return SB_OK;
+    SB_TRY(sb_cloud_alloc(c));
+    SB_TRY(sb_score_batch(c));
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->cl_rep, 0xFF, sizeof(int32_t) * (size_t)c->cl_max, c->stream));
+    SbProf prof(c, SB_PROF_CLOUD);
+    k_cloud_assign<<<1, 32, 0, c->stream>>>(c->hashes, c->counts, c->K, c->tree_begin, c->cl_hash_bits, c->cl_table,
+                                            c->cl_slots, c->cl_entries, c->cl_max, c->cl_meta, c->cl_assign, c->cl_rep,
+                                            c->cl_mismatch);
+    SB_TRY(sb_after_launch(c, "k_cloud_assign"));
+    const int64_t nchunks = sb_cdiv(c->n, 64);
+    size_t smem = sizeof(uint64_t) * 64 * (size_t)c->W;
+    if (smem > 48 * 1024)
+        SB_CHECK_CUDA(c, cudaFuncSetAttribute(k_cloud_verify, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_cloud_verify<<<(unsigned)nchunks, CLV_THREADS, smem, c->stream>>>(c->labels, c->n, c->W, c->flipw, c->K,
+                                                                         c->cl_assign, c->cl_rep, c->cl_bits,
+                                                                         c->cl_max, c->cl_mismatch);
+    SB_TRY(sb_after_launch(c, "k_cloud_verify"));
+    k_cloud_count<<<1, 1024, 0, c->stream>>>(c->cl_mismatch, c->K, c->cl_meta);
+    SB_TRY(sb_after_launch(c, "k_cloud_count"));
+    int32_t meta[4];
+    SB_CHECK_CUDA(c, cudaMemcpyAsync(meta, c->cl_meta, sizeof(meta), cudaMemcpyDeviceToHost, c->stream));
+    SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (meta[2] > 0) SB_TRY(cloud_resolve_collisions(c));
+    c->batch_in_cloud = true;
+    return SB_OK;
+}
+
+extern "C" sb_status sb_cloud_reset(sb_ctx* c, int64_t max_states, int32_t hash_bits)
+{
+    if (!c || max_states < 0 || max_states > (1ll << 30) || hash_bits < 0 || hash_bits > 64) return SB_ERR_ARG;
+    SB_CHECK_CUDA(c, cudaSetDevice(c->device));
+    SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+    sb_release_cloud(c);
+    c->cl_max = max_states > 0 ? max_states : CL_DEFAULT_STATES;
+    c->cl_hash_bits = hash_bits > 0 ? hash_bits : 64;
+    c->batch_in_cloud = true;  // a reset starts from the next sampled batch
+    if (c->has_graph) SB_TRY(sb_cloud_alloc(c));
+    return SB_OK;
+}
+
+extern "C" sb_status sb_cloud(sb_ctx* c, sb_cloud_entry* out, int64_t cap, int64_t* n_states_out, int32_t* fr_min_out)
+{
+    if (!c || cap < 0 || (cap > 0 && !out) || !n_states_out) return SB_ERR_ARG;
+    if (!c->has_graph) return sb_fail(c, SB_ERR_STATE, "no graph loaded");
+    SB_CHECK_CUDA(c, cudaSetDevice(c->device));
+    SB_TRY(sb_cloud_alloc(c));
+    if (c->has_batch && !c->batch_in_cloud) SB_TRY(sb_cloud_insert_batch(c));
+    int32_t meta[4];
+    SB_CHECK_CUDA(c, cudaMemcpyAsync(meta, c->cl_meta, sizeof(meta), cudaMemcpyDeviceToHost, c->stream));
+    SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int64_t ns = meta[0];
+    c->cl_n_host = ns;
+    *n_states_out = ns;
+    std::vector<sb_cloud_entry> host(ns > 0 ? ns : 1);
+    if (ns > 0)
+        SB_CHECK_CUDA(c, cudaMemcpy(host.data(), c->cl_entries, sizeof(sb_cloud_entry) * ns, cudaMemcpyDeviceToHost));
+    if (fr_min_out) {
+        int32_t mn = -1;
+        for (int64_t i = 0; i < ns; i++)
+            if (mn < 0 || host[i].S < mn) mn = host[i].S;
+        *fr_min_out = mn;
+    }
+    const int64_t k = std::min(ns, cap);
+    if (k > 0) SB_CHECK_CUDA(c, cudaMemcpy(out, host.data(), sizeof(sb_cloud_entry) * k, cudaMemcpyDefault));
+    if (meta[1] > 0) return sb_fail(c, SB_ERR_CLOUD_FULL, "cloud capacity %lld reached; %d trees not stored",
+                                    (long long)c->cl_max, meta[1]);
+    if (cap < ns && (cap > 0 || out))
+        return sb_fail(c, SB_ERR_CLOUD_FULL, "output capacity %lld < %lld states", (long long)cap, (long long)ns);
+    return SB_OK;
+}
+
+extern "C" sb_status sb_cloud_state(sb_ctx* c, int64_t idx, uint64_t* bits_out)
+{
+    if (!c || !bits_out) return SB_ERR_ARG;
+    if (!c->has_graph || !c->cl_table) return sb_fail(c, SB_ERR_STATE, "no cloud");
+    SB_CHECK_CUDA(c, cudaSetDevice(c->device));
+    if (c->has_batch && !c->batch_in_cloud) SB_TRY(sb_cloud_insert_batch(c));
+    int32_t ns = 0;
+    SB_CHECK_CUDA(c, cudaMemcpyAsync(&ns, c->cl_meta, sizeof(ns), cudaMemcpyDeviceToHost, c->stream));
+    SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (idx < 0 || idx >= ns) return sb_fail(c, SB_ERR_ARG, "state index %lld out of [0, %d)", (long long)idx, ns);
+    const int64_t nchunks = sb_cdiv(c->n, 64);
+    uint64_t* tmp = (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * (size_t)nchunks);
+    if (!tmp) return sb_fail(c, SB_ERR_OOM, "state export");
+    k_cloud_gather<<<(unsigned)std::min<int64_t>(sb_cdiv(nchunks, 256), 4096), 256, 0, c->stream>>>(
+        c->cl_bits, nchunks, c->cl_max, idx, tmp);
+    sb_status st = sb_after_launch(c, "k_cloud_gather");
+    if (st == SB_OK) st = sb_copy_out(c, bits_out, tmp, sizeof(uint64_t) * (size_t)nchunks);
+    cudaStreamSynchronize(c->stream);
+    sb_dfree(c, tmp);
+    return st;
+}

@@ -1,0 +1,229 @@
+// sb_internal.cuh -- context layout, device helpers and launch utilities
+// shared by the translation units of libsignedbal (CUDA, sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/signedbal.h"
+
+#define SB_WORDS_MAX 32          // 64-tree words processed per BFS launch
+#define SB_TREES_MAX (64 * 64)   // trees per sb_sample_trees call
+#define SB_BFS_CHUNK 256         // CSR entries per BFS work item
+#define SB_GL_CHUNK 256          // CSR entries per graphL work item
+#define SB_NEG_BIT 0x80000000u   // sign bit packed into CSR / edge-list ids
+#define SB_ID_MASK 0x7FFFFFFFu
+
+// -------------------------------------------------------------- hash rules
+// mix64: SplitMix64 output finaliser (Steele, Lea, Flood 2014).
+// fmix32: MurmurHash3 32-bit finaliser (Appleby).
+#define SB_GOLDEN 0x9E3779B97F4A7C15ULL
+#define SB_CHILD_SALT 0xD1B54A32D192ED03ULL
+#define SB_WEIGHT_SALT 0x6A09E667F3BCC909ULL
+
+__host__ __device__ __forceinline__ uint64_t sb_mix64(uint64_t z)
+{
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ULL;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    return z;
+}
+
+__host__ __device__ __forceinline__ uint32_t sb_fmix32(uint32_t h)
+{
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+__host__ __device__ __forceinline__ uint64_t sb_seed_key(uint64_t seed) { return sb_mix64(seed + SB_GOLDEN); }
+__host__ __device__ __forceinline__ uint64_t sb_tree_key(uint64_t S, int64_t t)
+{
+    return sb_mix64(S + ((uint64_t)t + 1u) * SB_GOLDEN);
+}
+__host__ __device__ __forceinline__ uint32_t sb_root(uint64_t K, int64_t n)
+{
+    return (uint32_t)(((K >> 32) * (uint64_t)n) >> 32);
+}
+__host__ __device__ __forceinline__ uint32_t sb_child_salt(uint64_t S, uint32_t v)
+{
+    return (uint32_t)(sb_mix64((uint64_t)v ^ S ^ SB_CHILD_SALT) >> 32);
+}
+__host__ __device__ __forceinline__ uint64_t sb_weight(uint32_t v) { return sb_mix64((uint64_t)v ^ SB_WEIGHT_SALT); }
+
+// ------------------------------------------------------------ context state
+struct sb_bfs_item {
+    int32_t v;     // vertex
+    int32_t beg;   // CSR range [beg, end)
+    int32_t end;
+    int32_t hub;   // -1 for a whole row, else index of the split row
+};
+
+struct sb_cloud_slot {
+    uint64_t key;   // table key (hash, possibly truncated)
+    int32_t state;  // index into entries, -1 = empty
+    int32_t pad;
+};
+
+struct sb_prof_rec {
+    cudaEvent_t a, b;
+    int fam;
+};
+
+struct sb_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    sb_alloc_fn alloc = nullptr;
+    sb_free_fn free_fn = nullptr;
+    void* alloc_user = nullptr;
+    char err[512] = {0};
+
+    // graph
+    bool has_graph = false;
+    int64_t n = 0, m = 0;
+    int2* edges = nullptr;        // m: (u, v | neg << 31), u < v, lexicographic
+    int32_t* rowptr = nullptr;    // n + 1
+    int32_t* col = nullptr;       // 2m: neighbour | neg << 31
+    sb_bfs_item* items = nullptr; // BFS work items
+    int64_t n_items = 0;
+    int32_t* hub_vertex = nullptr;  // split rows
+    int64_t n_hubs = 0;
+    sb_bfs_item* gl_items = nullptr; // graphL work items (hub = partial slot)
+    int64_t n_gl_items = 0;
+    int32_t* gl_hub_first = nullptr; // per split row: first partial slot
+    int32_t* gl_hub_vertex = nullptr;
+    int32_t* gl_hub_count = nullptr;
+    int64_t n_gl_hubs = 0, n_gl_partials = 0;
+    uint64_t* vweight = nullptr;  // n: state-hash weights
+
+    // last sampled batch
+    bool has_batch = false;
+    uint64_t seed = 0;
+    int64_t tree_begin = 0, K = 0;
+    int W = 0;                    // words = ceil(K / 64)
+    uint64_t* labels = nullptr;   // n x W raw labels (root label 0)
+    uint64_t* flipw = nullptr;    // W: label of vertex 0 per word (canonical flip)
+    uint64_t* hashes = nullptr;   // K
+    int32_t* counts = nullptr;    // K
+    bool counts_valid = false;
+    bool batch_in_cloud = false;
+    size_t labels_cap = 0;
+
+    // BFS scratch
+    uint64_t* vis = nullptr;
+    uint64_t* fr0 = nullptr;
+    uint64_t* fr1 = nullptr;
+    int32_t* done = nullptr;
+    uint64_t* hubnew = nullptr;
+    uint64_t* hubbest = nullptr;
+    uint32_t* sync = nullptr;     // [0..2] level counters, [4] barrier count, [5] barrier gen, [6] error
+    size_t bfs_cap_words = 0;
+
+    // cloud
+    int64_t cl_max = 0;
+    int64_t cl_slots = 0;
+    int32_t cl_hash_bits = 64;
+    sb_cloud_slot* cl_table = nullptr;
+    sb_cloud_entry* cl_entries = nullptr;
+    uint64_t* cl_bits = nullptr;   // [ceil(n/64)][cl_max] state bits, chunk-major
+    int32_t* cl_meta = nullptr;    // [0] n_states, [1] overflow, [2] mismatches
+    int32_t* cl_assign = nullptr;  // K: state per tree of the batch
+    int32_t* cl_rep = nullptr;     // cl_max: batch tree that created the state in this batch, else -1
+    int32_t* cl_mismatch = nullptr;// K
+    int64_t cl_n_host = 0;
+
+    // graphL scratch
+    float* gl_partial = nullptr;   // partial row sums of split rows
+    size_t gl_partial_cap = 0;
+    double* gl_red = nullptr;      // per-warp reduction partials
+    size_t gl_red_cap = 0;
+    float* gl_buf = nullptr;       // ping-pong buffer for descent
+    size_t gl_buf_cap = 0;
+    float* gl_scale = nullptr;     // per-column pending power-of-two scale
+    uint32_t* gl_colmax = nullptr;
+    int32_t* gl_misc = nullptr;
+    size_t gl_misc_cap = 0;
+
+    // misc scratch
+    void* tmp = nullptr;
+    size_t tmp_cap = 0;
+
+    // profiling: per-family launch counts, optional CUDA-event timing
+    int prof_on = 0;
+    int cur_family = SB_PROF_OTHER;
+    double prof_ms[SB_PROF_N] = {0};
+    int64_t prof_launch[SB_PROF_N] = {0};
+    std::vector<sb_prof_rec> prof_recs;
+    std::vector<cudaEvent_t> ev_pool;
+};
+
+// --------------------------------------------------------------- utilities
+sb_status sb_fail(sb_ctx* c, sb_status s, const char* fmt, ...);
+sb_status sb_cuda_fail(sb_ctx* c, cudaError_t e, const char* where);
+void* sb_dalloc(sb_ctx* c, size_t bytes);
+void sb_dfree(sb_ctx* c, void* p);
+// grows *p to at least `bytes` (contents not kept)
+sb_status sb_ensure(sb_ctx* c, void** p, size_t* cap, size_t bytes);
+bool sb_is_device_ptr(const void* p);
+sb_status sb_copy_out(sb_ctx* c, void* dst, const void* src_dev, size_t bytes);
+sb_status sb_after_launch(sb_ctx* c, const char* what);
+void sb_prof_begin(sb_ctx* c, cudaEvent_t* a);
+void sb_prof_end(sb_ctx* c, int fam, cudaEvent_t a);
+
+// Scope that attributes the kernel launches inside it to one family and,
+// when profiling is on, brackets them with CUDA events on the ctx stream.
+struct SbProf {
+    sb_ctx* c;
+    int fam, saved;
+    cudaEvent_t a;
+    SbProf(sb_ctx* cc, int f) : c(cc), fam(f), saved(cc->cur_family), a(nullptr)
+    {
+        c->cur_family = f;
+        sb_prof_begin(c, &a);
+    }
+    ~SbProf()
+    {
+        sb_prof_end(c, fam, a);
+        c->cur_family = saved;
+    }
+};
+void sb_release_graph(sb_ctx* c);
+void sb_release_batch(sb_ctx* c);
+void sb_release_cloud(sb_ctx* c);
+void sb_release_graphl(sb_ctx* c);
+
+// exclusive scan of n int32 values into out (int32); returns total via *total_dev (device int64*, nullable)
+sb_status sb_scan_i32(sb_ctx* c, const int32_t* in, int32_t* out, int64_t n, int64_t* total_dev);
+// LSD radix sort of uint64 keys over the low `bits` bits; result in keys
+sb_status sb_radix_sort_u64(sb_ctx* c, uint64_t* keys, int64_t n, int bits);
+
+// entry points implemented per translation unit
+sb_status sb_cloud_insert_batch(sb_ctx* c);
+sb_status sb_cloud_alloc(sb_ctx* c);
+sb_status sb_score_batch(sb_ctx* c);
+
+#define SB_CHECK_CUDA(ctx, call)                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return sb_cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+#define SB_TRY(call)                      \
+    do {                                  \
+        sb_status s_ = (call);            \
+        if (s_ != SB_OK) return s_;       \
+    } while (0)
+
+__host__ __device__ __forceinline__ int64_t sb_cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+__device__ __forceinline__ unsigned sb_lane() { return threadIdx.x & 31u; }

@@ -1,0 +1,340 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+graphBpp results are integers and must match bit for bit (trees, labels,
+counts, hashes, cloud).  graphL runs in float32 against the oracle's float64
+with the tolerances derived in the design notes (C10 reading).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2311_00869_gb300 as P
+
+    return P
+
+
+@pytest.fixture()
+def sb(P):
+    s = P.SignedBal(0)
+    yield s
+    s.close()
+
+
+def load_both(sb, n, u, v, s, flags=O.LOAD_LCC | O.LOAD_MERGE_DUP):
+    g = O.clean_graph(n, u, v, s, flags)
+    n1, m1, vmap = sb.load_graph(n, u, v, s, flags, want_vmap=True)
+    assert (n1, m1) == (g.n, g.m)
+    assert np.array_equal(vmap, g.vmap)
+    return g
+
+
+def check_batch(P, sb, g, seed, t0, K, parents=False, labels=True):
+    par = sb.sample_trees(seed, t0, K, want_parents=parents)
+    counts, hashes = sb.frustration()
+    ref = O.sample(g, seed, t0, K, want_labels=labels, want_parents=parents)
+    assert np.array_equal(counts.cpu().numpy(), ref["counts"])
+    assert np.array_equal(hashes.cpu().numpy().view(np.uint64), ref["hashes"])
+    if parents:
+        assert np.array_equal(par.cpu().numpy(), ref["parents"])
+    if labels:
+        lab = P.unpack_labels(sb.label(), K)
+        assert np.array_equal(lab, ref["labels"])
+    return ref
+
+
+# ------------------------------------------------------------------ ingest
+
+@pytest.mark.parametrize("case", range(4))
+def test_ingest_matches_oracle(sb, case):
+    rng = np.random.Generator(np.random.PCG64(50 + case))
+    n = 300 + 200 * case
+    m = 2 * n
+    a = rng.integers(0, n, m)
+    b = rng.integers(0, n, m)
+    keep = a != b
+    a, b = a[keep], b[keep]
+    # repeat some pairs, reversed, with the same sign (merged duplicates)
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    key, idx = np.unique(lo * n + hi, return_index=True)
+    a, b = a[idx], b[idx]
+    s = np.where(rng.random(a.shape[0]) < 0.3, -1, 1).astype(np.int8)
+    rep = rng.integers(0, a.shape[0], a.shape[0] // 5)
+    a2 = np.concatenate([a, b[rep]]).astype(np.int32)
+    b2 = np.concatenate([b, a[rep]]).astype(np.int32)
+    s2 = np.concatenate([s, s[rep]]).astype(np.int8)
+    g = load_both(sb, n, a2, b2, s2)
+    u, v, neg = (t.cpu().numpy() for t in sb.graph_edges())
+    assert np.array_equal(u, g.eu) and np.array_equal(v, g.ev) and np.array_equal(neg, g.eneg)
+    rp, col, cneg = (t.cpu().numpy() for t in sb.graph_csr())
+    assert np.array_equal(rp, g.rowptr.astype(np.int32))
+    assert np.array_equal(col, g.col) and np.array_equal(cneg, g.colneg)
+
+
+def test_ingest_from_device_and_pinned_host(sb):
+    n, u, v, s = synth.er_graph(400, 1600, 0.3, seed=3)
+    g = O.clean_graph(n, u, v, s)
+    for conv in (lambda x: torch.from_numpy(x).cuda(), lambda x: torch.from_numpy(x).pin_memory()):
+        n1, m1, _ = sb.load_graph(n, conv(u), conv(v), conv(s))
+        assert (n1, m1) == (g.n, g.m)
+        uu, vv, nn = (t.cpu().numpy() for t in sb.graph_edges())
+        assert np.array_equal(uu, g.eu) and np.array_equal(vv, g.ev) and np.array_equal(nn, g.eneg)
+
+
+def test_ingest_errors_match_oracle(P, sb):
+    cases = [
+        (3, [0, 1], [1, 1], [1, 1], 3),
+        (3, [0, 1], [1, 2], [1, 0], 3),
+        (3, [0, 1], [1, 3], [1, 1], 3),
+        (3, [0, 1, 1], [1, 2, 0], [1, 1, -1], 3),
+        (3, [0, 1, 1], [1, 2, 0], [1, 1, 1], O.LOAD_LCC),
+        (4, [0, 2], [1, 3], [1, 1], O.LOAD_MERGE_DUP),
+        (3, [0, 1, 1, 2], [2, 1, 0, 5], [7, 1, 1, 1], 3),  # first bad edge decides
+    ]
+    for n, a, b, s, flags in cases:
+        a = np.array(a, np.int32)
+        b = np.array(b, np.int32)
+        s = np.array(s, np.int8)
+        with pytest.raises(O.OracleError) as eo:
+            O.clean_graph(n, a, b, s, flags)
+        with pytest.raises(P.SignedBalError) as eg:
+            sb.load_graph(n, a, b, s, flags)
+        assert eg.value.code == eo.value.code
+
+
+def test_single_vertex_and_single_edge(P, sb):
+    g = load_both(sb, 5, np.array([], np.int32), np.array([], np.int32), np.array([], np.int8))
+    assert g.n == 1 and g.m == 0
+    check_batch(P, sb, g, 0, 0, 3, parents=True)
+    g = load_both(sb, 2, np.array([1], np.int32), np.array([0], np.int32), np.array([-1], np.int8))
+    check_batch(P, sb, g, 9, 5, 70, parents=True)
+
+
+# ------------------------------------------------------------------ graphBpp
+
+@pytest.mark.parametrize("K", [1, 63, 64, 130])
+def test_trees_labels_counts_small(P, sb, K):
+    n, u, v, s = synth.random_connected(60, 90, seed=K)
+    g = load_both(sb, n, u, v, s)
+    check_batch(P, sb, g, seed=K + 1, t0=7, K=K, parents=True)
+
+
+def test_split_rows_hub(P, sb):
+    # vertex 0 joins 700 others (split into several chunks) plus a random mesh
+    rng = np.random.Generator(np.random.PCG64(77))
+    n = 701
+    a = np.concatenate([np.zeros(700, np.int64), rng.integers(1, n, 900)])
+    b = np.concatenate([np.arange(1, n), rng.integers(1, n, 900)])
+    keep = a != b
+    a, b = a[keep].astype(np.int32), b[keep].astype(np.int32)
+    s = np.where(rng.random(a.shape[0]) < 0.35, -1, 1).astype(np.int8)
+    g = load_both(sb, n, a, b, s)
+    assert np.diff(g.rowptr).max() > 512
+    check_batch(P, sb, g, seed=5, t0=0, K=200, parents=True)
+    check_batch(P, sb, g, seed=6, t0=0, K=2048 + 33, parents=False)
+
+
+def test_config1_plain_equals_batched_and_oracle(P, sb):
+    n, u, v, s = synth.er_graph()
+    g = load_both(sb, n, u, v, s)
+    ref = check_batch(P, sb, g, seed=0, t0=0, K=64, parents=True)
+    cl, fr = sb.cloud()
+    rc = O.cloud(ref["labels"], ref["counts"])
+    assert np.array_equal(cl["first_tree"], rc["first_tree"])
+    assert np.array_equal(cl["count"], rc["count"])
+    assert np.array_equal(cl["S"], rc["S"])
+    assert np.array_equal(cl["hash"], rc["H"])
+    assert fr == rc["S"].min()
+    # plain path: one tree per call, cloud accumulated over 64 calls
+    sb.cloud_reset()
+    for t in range(64):
+        sb.sample_trees(0, t, 1)
+        c1, h1 = sb.frustration()
+        assert c1.item() == ref["counts"][t]
+        sb.cloud()
+    cl2, fr2 = sb.cloud()
+    for k in ("first_tree", "count", "S", "hash"):
+        assert np.array_equal(cl2[k], cl[k])
+
+
+def test_rmat_multiword_ragged(P, sb):
+    n, u, v, s = synth.rmat_two_faction(scale=13, m_target=1 << 16, seed=12)
+    g = load_both(sb, n, u, v, s)
+    K = 32 * 64 + 52  # two BFS launches, ragged last word
+    sb.sample_trees(11, 1000, K)
+    counts, hashes = sb.frustration()
+    ref = O.sample(g, 11, 1000, K, want_labels=True)
+    assert np.array_equal(counts.cpu().numpy(), ref["counts"])
+    assert np.array_equal(hashes.cpu().numpy().view(np.uint64), ref["hashes"])
+    lab = P.unpack_labels(sb.label(), K)
+    assert np.array_equal(lab, ref["labels"])
+
+
+def test_determinism_repeat(P, sb):
+    n, u, v, s = synth.rmat_two_faction(scale=12, m_target=1 << 15, seed=3)
+    sb.load_graph(n, u, v, s)
+    outs = []
+    for _ in range(2):
+        sb.sample_trees(4, 0, 1000)
+        c, h = sb.frustration()
+        outs.append((c.cpu().numpy(), h.cpu().numpy(), sb.label().cpu().numpy()))
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------------- cloud
+
+def test_cloud_balanced_graph_single_state(P, sb):
+    n, u, v, s, side = synth.planted_balanced(500, 900, seed=8)
+    g = load_both(sb, n, u, v, s)
+    sb.sample_trees(1, 0, 300)
+    counts, _ = sb.frustration()
+    assert int(counts.max()) == 0
+    cl, fr = sb.cloud()
+    assert cl["S"].tolist() == [0] and cl["count"].tolist() == [300] and fr == 0
+    bits = sb.cloud_state(0).cpu().numpy().view(np.uint64)
+    lab = ((bits[np.arange(g.n) // 64] >> (np.arange(g.n) % 64).astype(np.uint64)) & np.uint64(1)).astype(np.int8)
+    assert np.array_equal(lab, (side ^ side[0]).astype(np.int8))
+
+
+@pytest.mark.parametrize("hash_bits", [64, 3])
+def test_cloud_accumulates_and_checks_collisions(P, sb, hash_bits):
+    # a small graph with few distinct states so trees repeat states
+    n, u, v, s = synth.random_connected(12, 5, seed=21)
+    g = load_both(sb, n, u, v, s)
+    sb.cloud_reset(0, hash_bits)
+    K = 150
+    for t0 in (0, K, 2 * K):
+        sb.sample_trees(2, t0, K)
+        sb.cloud()
+    cl, fr = sb.cloud()
+    ref = O.sample(g, 2, 0, 3 * K)
+    rc = O.cloud(ref["labels"], ref["counts"])
+    assert np.array_equal(cl["first_tree"], rc["first_tree"])
+    assert np.array_equal(cl["count"], rc["count"])
+    assert np.array_equal(cl["S"], rc["S"])
+    assert np.array_equal(cl["hash"], rc["H"])
+    for i, f in enumerate(rc["first_tree"]):
+        bits = sb.cloud_state(i).cpu().numpy().view(np.uint64)
+        lab = ((bits[np.arange(g.n) // 64] >> (np.arange(g.n) % 64).astype(np.uint64)) & np.uint64(1)).astype(np.uint8)
+        assert np.array_equal(lab, ref["labels"][f])
+
+
+def test_cloud_capacity_error(P, sb):
+    n, u, v, s = synth.random_connected(40, 60, seed=4)
+    load_both(sb, n, u, v, s)
+    sb.cloud_reset(2, 0)
+    sb.sample_trees(0, 0, 64)
+    with pytest.raises(P.SignedBalError) as e:
+        sb.cloud(cap=2)
+    assert e.value.code == -11
+
+
+# ------------------------------------------------------------------ graphL
+
+def _hub_graph(seed=31, n=900):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    a = np.concatenate([np.zeros(n - 1, np.int64), rng.integers(1, n, 2 * n)])
+    b = np.concatenate([np.arange(1, n), rng.integers(1, n, 2 * n)])
+    keep = a != b
+    a, b = a[keep].astype(np.int32), b[keep].astype(np.int32)
+    s = np.where(rng.random(a.shape[0]) < 0.3, -1, 1).astype(np.int8)
+    return n, a, b, s
+
+
+@pytest.mark.parametrize("R", [3, 8, 256])
+def test_graphl_fwd_bwd_against_fp64(P, sb, R):
+    n, a, b, s = _hub_graph()
+    g = load_both(sb, n, a, b, s)
+    gam = synth.gamma0(g.n, R, seed=R)
+    G = torch.from_numpy(gam).cuda()
+    loss, F = sb.graphL_fwd(G)
+    L64, F64 = O.graphl_loss_f64(g, gam.astype(np.float64))
+    assert np.array_equal(F.cpu().numpy(), F64)
+    prod = np.abs(gam[g.eu].astype(np.float64) * gam[g.ev])
+    bound = 1e-5 * (0.5 * (1.0 + prod)).sum(axis=0)
+    assert np.all(np.abs(loss.cpu().numpy().astype(np.float64) - L64) <= bound)
+    gout = torch.linspace(0.5, 1.5, R, device="cuda")
+    grad = sb.graphL_bwd(G, gout).cpu().numpy().astype(np.float64)
+    ref = O.graphl_grad_f64(g, gam.astype(np.float64), gout.cpu().numpy().astype(np.float64))
+    assert np.linalg.norm(grad - ref) <= 1e-5 * np.linalg.norm(ref)
+    absnb = np.zeros((g.n, R))
+    np.add.at(absnb, g.eu, np.abs(gam[g.ev]))
+    np.add.at(absnb, g.ev, np.abs(gam[g.eu]))
+    comp_bound = 1e-5 * 0.5 * absnb * np.abs(gout.cpu().numpy())[None, :] + 1e-30
+    assert np.all(np.abs(grad - ref) <= comp_bound)
+    # bitwise reproducible
+    assert torch.equal(sb.graphL_bwd(G, gout), sb.graphL_bwd(G, gout))
+
+
+def test_graphl_autograd_function(P, sb):
+    n, a, b, s = _hub_graph(seed=5, n=300)
+    g = load_both(sb, n, a, b, s)
+    gam = synth.gamma0(g.n, 4, seed=1)
+    G = torch.from_numpy(gam).cuda().requires_grad_(True)
+    loss = P.GraphLLoss.apply(G, sb)
+    (loss * torch.tensor([1.0, 2.0, 3.0, 4.0], device="cuda")).sum().backward()
+    ref = O.graphl_grad_f64(g, gam.astype(np.float64), np.array([1.0, 2.0, 3.0, 4.0]))
+    got = G.grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_graphl_descent_and_round(P, sb):
+    n, a, b, s = _hub_graph(seed=9, n=600)
+    g = load_both(sb, n, a, b, s)
+    R, steps, alpha = 8, 40, 0.05
+    gam = synth.gamma0(g.n, R, seed=2)
+    G0 = torch.from_numpy(gam).cuda()
+    out, exps, F_trace, F_final = sb.graphL_descent(G0, alpha, steps, renorm_log2=32, trace=True)
+    ref, rexps, rtrace = O.graphl_descent_f64(g, gam, alpha, steps, renorm_log2=32, trace=True)
+    e = exps.cpu().numpy()
+    assert np.all(e > 0)  # the hub makes the update grow past 2^32
+    got = out.cpu().numpy().astype(np.float64) * np.exp2(e.astype(np.float64))[None, :]
+    want = ref * np.exp2(rexps.astype(np.float64))[None, :]
+    scale = np.abs(want).max(axis=0)
+    assert np.all(np.abs(got - want) <= 1e-3 * scale[None, :])
+    # the first trace entry is the discrete loss of the start point, exactly
+    assert np.array_equal(F_trace.cpu().numpy()[0], rtrace[0])
+    # rounding: GPU and oracle agree exactly on the same float32 state
+    Fr, flip = sb.graphL_round(out, want_flip=True)
+    oF, oflip = O.graphl_round_f32(g, out.cpu().numpy(), want_flip=True)
+    assert np.array_equal(Fr.cpu().numpy(), oF)
+    assert np.array_equal(F_final.cpu().numpy(), oF)
+    fw = flip.cpu().numpy().view(np.uint64)
+    bits = ((fw[:, np.arange(g.m) // 64] >> (np.arange(g.m) % 64).astype(np.uint64)) & np.uint64(1)).astype(np.uint8)
+    assert np.array_equal(bits, oflip)
+    # final signs agree with the float64 run except where the value is tiny
+    dis = np.sign(got) != np.sign(want)
+    assert np.all(np.abs(want[dis]) <= 1e-3 * scale[np.nonzero(dis)[1]])
+
+
+# ------------------------------------------------- full size, sampled trees
+
+def test_rmat_2pow20_sampled_trees(P, sb):
+    """The 2^20-vertex, 2^24-edge two-faction R-MAT graph in the benchmark's
+    launch configuration (K = 1024 trees in one batch): trees 0 and 1023 are
+    checked against the oracle bit for bit; every count is checked against
+    the bound given by its own labels."""
+    n, u, v, s = synth.rmat_two_faction(scale=20, m_target=1 << 24)
+    n1, m1, _ = sb.load_graph(n, u, v, s)
+    g = O.clean_graph(n, u, v, s)
+    assert (n1, m1) == (g.n, g.m)
+    K = 1024
+    sb.sample_trees(0, 0, K)
+    counts, hashes = sb.frustration()
+    counts, hashes = counts.cpu().numpy(), hashes.cpu().numpy().view(np.uint64)
+    labw = sb.label().cpu().numpy().view(np.uint64)
+    for t in (0, K - 1):
+        ref = O.sample(g, 0, t, 1)
+        assert counts[t] == ref["counts"][0]
+        assert hashes[t] == ref["hashes"][0]
+        lab = ((labw[:, t // 64] >> np.uint64(t % 64)) & np.uint64(1)).astype(np.uint8)
+        assert np.array_equal(lab, ref["labels"][0])
+    assert np.all(counts >= 0) and np.all(counts <= g.m - g.n + 1)
