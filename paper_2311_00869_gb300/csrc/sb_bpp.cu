@@ -81,14 +81,66 @@ __device__ __forceinline__ unsigned group_mask(int G)
     return ((1u << G) - 1u) << base;
 }
 
+// One pass over a CSR range for one (vertex, word) lane, 8 neighbours at a
+// time so that 8 frontier gathers are in flight per lane.
+//   HASH = false: once / twice = trees reached through >= 1 / >= 2 candidates,
+//                 labx = candidate label bits (exact where once & ~twice).
+//   HASH = true : argmin of the hashed parent key over candidates in `mask`;
+//                 once = trees seen, labx = winners' label bits, best / bestu
+//                 hold the winners' hash / id in shared memory.
+// `cur` and `lab` are rewritten between levels by other blocks, so they are
+// read with plain (coherent) loads; the column array is read-only.
+template <bool HASH, bool PAR, int BD>
+__device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint64_t* cur, const uint64_t* lab, int Wb,
+                                         int Wt, int wofs, int gl, uint64_t mask, uint32_t y, const uint32_t* akey_w,
+                                         uint32_t* best, int32_t* bestu, int tid, uint64_t& once, uint64_t& twice,
+                                         uint64_t& labx)
+{
+    for (int j = 0; j < len; j += 8) {
+        uint32_t c[8];
+        uint64_t f[8], l[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) c[k] = (j + k < len) ? (uint32_t)__ldg(cp + j + k) : 0u;
+#pragma unroll
+        for (int k = 0; k < 8; k++) f[k] = (j + k < len) ? (cur[(int64_t)(c[k] & SB_ID_MASK) * Wb + gl] & mask) : 0ull;
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            l[k] = f[k] ? (lab[(int64_t)(c[k] & SB_ID_MASK) * Wt + wofs] ^ ((c[k] >> 31) ? ~0ull : 0ull)) : 0ull;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if (!HASH) {
+                twice |= once & f[k];
+                once |= f[k];
+                labx |= f[k] & l[k];
+            } else {
+                uint64_t b = f[k];
+                const uint32_t u = c[k] & SB_ID_MASK;
+                const uint32_t hx = u ^ y;
+                while (b) {
+                    const int t = __ffsll((long long)b) - 1;
+                    const uint64_t bit = 1ull << t;
+                    b &= b - 1;
+                    const uint32_t h = sb_fmix32(hx + akey_w[t]);
+                    if (!(once & bit) || h < best[t * BD + tid]) {
+                        once |= bit;
+                        best[t * BD + tid] = h;
+                        labx = (labx & ~bit) | (l[k] & bit);
+                        if (PAR) bestu[t * BD + tid] = (int32_t)u;
+                    }
+                }
+            }
+        }
+    }
+}
+
 template <int G, bool PAR>
 __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
     k_bfs(BfsArgs A)
 {
     constexpr int BD = PAR ? BFS_THREADS_PAR : BFS_THREADS;
     extern __shared__ uint32_t smem[];
-    uint32_t* akey = smem;                 // Wb * 64 tree salts
-    uint32_t* best = smem + SB_WORDS_MAX * 64;  // 64 x BD running minima
+    uint32_t* akey = smem;                        // Wb * 64 tree salts
+    uint32_t* best = smem + SB_WORDS_MAX * 64;    // 64 x BD running minima
     int32_t* bestu = (int32_t*)(best + 64 * BD);  // 64 x BD winners (PAR only)
     __shared__ uint32_t s_any;
 
@@ -105,10 +157,12 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
     __syncthreads();
 
     const int Wb = A.Wb, Wt = A.Wt, w0 = A.w0;
+    const int wofs = w0 + gl;
+    const uint32_t* akey_w = akey + gl * 64;
     int L = 1;
     while (true) {
-        const uint64_t* __restrict__ cur = (L & 1) ? A.fr0 : A.fr1;
-        uint64_t* __restrict__ nxt = (L & 1) ? A.fr1 : A.fr0;
+        const uint64_t* cur = (L & 1) ? A.fr0 : A.fr1;
+        uint64_t* nxt = (L & 1) ? A.fr1 : A.fr0;
         bool any_new = false;
 
         // ---- phase A: every work item (whole rows, and chunks of split rows)
@@ -121,86 +175,51 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
             const uint64_t U = ~vis_w;
             const int32_t* cp = A.col + itm.beg;
             const int len = itm.end - itm.beg;
-            if (itm.hub >= 0) {
-                // chunk of a split row: candidates merge through global atomics
-                if (U) {
-                    const uint32_t y = sb_child_salt(A.S, (uint32_t)v);
-                    uint64_t acc = 0;
-                    uint64_t* hb = A.hubbest + ((int64_t)itm.hub * Wb + gl) * 64;
-                    for (int j = 0; j < len; j++) {
-                        const uint32_t c = (uint32_t)cp[j];
-                        const uint32_t u = c & SB_ID_MASK;
-                        uint64_t f = cur[(int64_t)u * Wb + gl] & U;
-                        if (f) {
-                            acc |= f;
-                            const uint64_t lu = A.lab[(int64_t)u * Wt + w0 + gl] ^ ((c >> 31) ? ~0ull : 0ull);
-                            const uint32_t hx = u ^ y;
-                            while (f) {
-                                const int t = __ffsll((long long)f) - 1;
-                                f &= f - 1;
-                                const uint32_t h = sb_fmix32(hx + akey[gl * 64 + t]);
-                                const unsigned long long key =
-                                    ((unsigned long long)h << 32) | ((unsigned long long)u << 1) | ((lu >> t) & 1ull);
-                                atomicMin((unsigned long long*)(hb + t), key);
-                            }
-                        }
-                    }
-                    if (acc) atomicOr((unsigned long long*)(A.hubnew + (int64_t)itm.hub * Wb + gl), acc);
-                }
-                continue;
-            }
+            const bool hub = itm.hub >= 0;
             uint64_t once = 0, twice = 0, labx = 0;
             if (U) {
-#pragma unroll 4
-                for (int j = 0; j < len; j++) {
-                    const uint32_t c = (uint32_t)cp[j];
-                    const uint32_t u = c & SB_ID_MASK;
-                    const uint64_t f = cur[(int64_t)u * Wb + gl] & U;
-                    if (f) {
-                        const uint64_t lu = A.lab[(int64_t)u * Wt + w0 + gl] ^ ((c >> 31) ? ~0ull : 0ull);
-                        twice |= once & f;
-                        once |= f;
-                        labx |= f & lu;
+                const uint32_t y = sb_child_salt(A.S, (uint32_t)v);
+                if (!hub && !PAR) {
+                    scan_row<false, PAR, BD>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, akey_w, best, bestu, tid,
+                                             once, twice, labx);
+                    if (twice) {
+                        // trees reached through two or more candidates: hashed argmin
+                        uint64_t o2 = 0, t2 = 0, l2 = 0;
+                        scan_row<true, PAR, BD>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, twice, y, akey_w, best, bestu,
+                                                tid, o2, t2, l2);
+                        labx = (labx & ~twice) | (l2 & twice);
                     }
+                } else {
+                    scan_row<true, PAR, BD>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, akey_w, best, bestu, tid,
+                                            once, twice, labx);
                 }
             }
-            // trees reached through two or more candidates need the hashed argmin
-            const uint64_t multi = PAR ? once : twice;
-            if (multi) {
-                const uint32_t y = sb_child_salt(A.S, (uint32_t)v);
-                uint64_t labm = 0, seen = 0;
-                for (int j = 0; j < len; j++) {
-                    const uint32_t c = (uint32_t)cp[j];
-                    const uint32_t u = c & SB_ID_MASK;
-                    uint64_t f = cur[(int64_t)u * Wb + gl] & multi;
-                    if (f) {
-                        const uint64_t lu = A.lab[(int64_t)u * Wt + w0 + gl] ^ ((c >> 31) ? ~0ull : 0ull);
-                        const uint32_t hx = u ^ y;
-                        while (f) {
-                            const int t = __ffsll((long long)f) - 1;
-                            f &= f - 1;
-                            const uint32_t h = sb_fmix32(hx + akey[gl * 64 + t]);
-                            if (!((seen >> t) & 1ull) || h < best[t * BD + tid]) {
-                                seen |= 1ull << t;
-                                best[t * BD + tid] = h;
-                                labm = (labm & ~(1ull << t)) | (((lu >> t) & 1ull) << t);
-                                if (PAR) bestu[t * BD + tid] = (int32_t)u;
-                            }
-                        }
-                    }
-                }
-                labx = (labx & ~multi) | (labm & multi);
-                if (PAR && A.parents) {
+            if (hub) {
+                // chunk of a split row: publish the chunk minima, one atomic per tree
+                if (once) {
+                    uint64_t* hb = A.hubbest + ((int64_t)itm.hub * Wb + gl) * 64;
                     for (uint64_t b = once; b;) {
                         const int t = __ffsll((long long)b) - 1;
                         b &= b - 1;
-                        A.parents[(64 * (int64_t)(w0 + gl) + t) * A.n + v] = bestu[t * BD + tid];
+                        const unsigned long long key = ((unsigned long long)best[t * BD + tid] << 32) |
+                                                       (PAR ? ((unsigned long long)(uint32_t)bestu[t * BD + tid] << 1) : 0ull) |
+                                                       ((labx >> t) & 1ull);
+                        atomicMin((unsigned long long*)(hb + t), key);
                     }
+                    atomicOr((unsigned long long*)(A.hubnew + (int64_t)itm.hub * Wb + gl), once);
+                }
+                continue;
+            }
+            if (PAR && A.parents) {
+                for (uint64_t b = once; b;) {
+                    const int t = __ffsll((long long)b) - 1;
+                    b &= b - 1;
+                    A.parents[(64 * (int64_t)wofs + t) * A.n + v] = bestu[t * BD + tid];
                 }
             }
             if (act) {
                 if (once) {
-                    A.lab[(int64_t)v * Wt + w0 + gl] |= labx & once;
+                    A.lab[(int64_t)v * Wt + wofs] |= labx & once;
                     A.vis[(int64_t)v * Wb + gl] = vis_w | once;
                     any_new = true;
                 }
@@ -235,10 +254,10 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
                         hb[t] = ~0ull;
                         labx |= (key & 1ull) << t;
                         if (PAR && A.parents)
-                            A.parents[(64 * (int64_t)(w0 + gl) + t) * A.n + v] = (int32_t)((key >> 1) & SB_ID_MASK);
+                            A.parents[(64 * (int64_t)wofs + t) * A.n + v] = (int32_t)((key >> 1) & SB_ID_MASK);
                     }
                     if (nw) {
-                        A.lab[(int64_t)v * Wt + w0 + gl] |= labx;
+                        A.lab[(int64_t)v * Wt + wofs] |= labx;
                         A.vis[(int64_t)v * Wb + gl] = vis_w | nw;
                         any_new = true;
                     }

@@ -322,9 +322,20 @@ extern "C" sb_status sb_cloud(sb_ctx* c, sb_cloud_entry* out, int64_t cap, int64
     const int64_t ns = meta[0];
     c->cl_n_host = ns;
     *n_states_out = ns;
+    const bool full = meta[1] > 0;
+    if (!out && !fr_min_out)  // insertion only
+        return full ? sb_fail(c, SB_ERR_CLOUD_FULL, "cloud capacity %lld reached; %d trees not stored",
+                              (long long)c->cl_max, meta[1])
+                    : SB_OK;
     std::vector<sb_cloud_entry> host(ns > 0 ? ns : 1);
     if (ns > 0)
         SB_CHECK_CUDA(c, cudaMemcpy(host.data(), c->cl_entries, sizeof(sb_cloud_entry) * ns, cudaMemcpyDeviceToHost));
+    // order of first appearance (states created on the collision path are
+    // numbered after the states of later trees of their batch)
+    c->cl_order.resize(ns);
+    for (int64_t i = 0; i < ns; i++) c->cl_order[i] = (int32_t)i;
+    std::stable_sort(c->cl_order.begin(), c->cl_order.end(),
+                     [&](int32_t a, int32_t b) { return host[a].first_tree < host[b].first_tree; });
     if (fr_min_out) {
         int32_t mn = -1;
         for (int64_t i = 0; i < ns; i++)
@@ -332,9 +343,14 @@ extern "C" sb_status sb_cloud(sb_ctx* c, sb_cloud_entry* out, int64_t cap, int64
         *fr_min_out = mn;
     }
     const int64_t k = std::min(ns, cap);
-    if (k > 0) SB_CHECK_CUDA(c, cudaMemcpy(out, host.data(), sizeof(sb_cloud_entry) * k, cudaMemcpyDefault));
-    if (meta[1] > 0) return sb_fail(c, SB_ERR_CLOUD_FULL, "cloud capacity %lld reached; %d trees not stored",
-                                    (long long)c->cl_max, meta[1]);
+    if (k > 0) {
+        std::vector<sb_cloud_entry> sorted(k);
+        for (int64_t i = 0; i < k; i++) sorted[i] = host[c->cl_order[i]];
+        SB_CHECK_CUDA(c, cudaMemcpy(out, sorted.data(), sizeof(sb_cloud_entry) * k, cudaMemcpyDefault));
+    }
+    if (full)
+        return sb_fail(c, SB_ERR_CLOUD_FULL, "cloud capacity %lld reached; %d trees not stored", (long long)c->cl_max,
+                       meta[1]);
     if (cap < ns && (cap > 0 || out))
         return sb_fail(c, SB_ERR_CLOUD_FULL, "output capacity %lld < %lld states", (long long)cap, (long long)ns);
     return SB_OK;
@@ -350,6 +366,15 @@ extern "C" sb_status sb_cloud_state(sb_ctx* c, int64_t idx, uint64_t* bits_out)
     SB_CHECK_CUDA(c, cudaMemcpyAsync(&ns, c->cl_meta, sizeof(ns), cudaMemcpyDeviceToHost, c->stream));
     SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
     if (idx < 0 || idx >= ns) return sb_fail(c, SB_ERR_ARG, "state index %lld out of [0, %d)", (long long)idx, ns);
+    if ((int64_t)c->cl_order.size() != ns) {
+        std::vector<sb_cloud_entry> host(ns);
+        SB_CHECK_CUDA(c, cudaMemcpy(host.data(), c->cl_entries, sizeof(sb_cloud_entry) * ns, cudaMemcpyDeviceToHost));
+        c->cl_order.resize(ns);
+        for (int64_t i = 0; i < ns; i++) c->cl_order[i] = (int32_t)i;
+        std::stable_sort(c->cl_order.begin(), c->cl_order.end(),
+                         [&](int32_t a, int32_t b) { return host[a].first_tree < host[b].first_tree; });
+    }
+    idx = c->cl_order[idx];
     const int64_t nchunks = sb_cdiv(c->n, 64);
     uint64_t* tmp = (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * (size_t)nchunks);
     if (!tmp) return sb_fail(c, SB_ERR_OOM, "state export");

@@ -210,6 +210,7 @@ void sb_release_cloud(sb_ctx* c)
     SB_FREE(cl_mismatch);
     c->cl_slots = 0;
     c->cl_n_host = 0;
+    c->cl_order.clear();
 }
 
 void sb_release_graphl(sb_ctx* c)

@@ -62,13 +62,16 @@ __device__ __forceinline__ void gl_emit(const GlArgs& A, int64_t v, int r, float
     }
 }
 
-// Rows (and chunks of split rows): one warp per (item, segment of 32*VEC columns).
-template <int VEC, bool STEP>
+// Rows (and chunks of split rows): a sub-warp of SL lanes per (item, segment
+// of SL*VEC columns).  Units run segment-major, so one segment's columns of G
+// (n x SL*VEC floats; 84 MB for 656k vertices at 32 columns) stay in L2 while
+// every row gathers from them.
+template <int VEC, int SL, bool STEP>
 __global__ void __launch_bounds__(GL_THREADS) k_gl_rows(GlArgs A)
 {
     extern __shared__ uint32_t gsm[];
-    int32_t* sF = (int32_t*)gsm;          // R
-    uint32_t* smax = gsm + A.R;           // R
+    int32_t* sF = (int32_t*)gsm;  // R
+    uint32_t* smax = gsm + A.R;   // R
     const int R = A.R;
     if (STEP) {
         for (int i = threadIdx.x; i < R; i += GL_THREADS) {
@@ -78,17 +81,19 @@ __global__ void __launch_bounds__(GL_THREADS) k_gl_rows(GlArgs A)
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
-    const int64_t warps_total = (int64_t)gridDim.x * (GL_THREADS / 32);
-    const int64_t warp_id = (int64_t)blockIdx.x * (GL_THREADS / 32) + (threadIdx.x >> 5);
-    const int seg_w = 32 * VEC;
+    const int sl = lane & (SL - 1);
+    const unsigned smask = SL == 32 ? 0xffffffffu : (((1u << SL) - 1u) << (lane & ~(SL - 1)));
+    const int64_t subs_total = (int64_t)gridDim.x * (GL_THREADS / SL);
+    const int64_t sub_id = (int64_t)blockIdx.x * (GL_THREADS / SL) + threadIdx.x / SL;
+    constexpr int seg_w = SL * VEC;
     const int nseg = (R + seg_w - 1) / seg_w;
     const int64_t units = A.n_items * nseg;
     const bool wantF = STEP && A.F != nullptr;
-    for (int64_t u = warp_id; u < units; u += warps_total) {
+    for (int64_t u = sub_id; u < units; u += subs_total) {
         const int seg = (int)(u / A.n_items);
         const int64_t it = u - (int64_t)seg * A.n_items;
         const sb_bfs_item itm = A.items[it];
-        const int r0 = seg * seg_w + lane * VEC;
+        const int r0 = seg * seg_w + sl * VEC;
         const bool act = r0 < R;
         float acc[VEC], blk[VEC];
         int32_t fcnt[VEC];
@@ -100,38 +105,41 @@ __global__ void __launch_bounds__(GL_THREADS) k_gl_rows(GlArgs A)
             sv[k] = 0;
         }
         if (wantF && act) {
-            // sign bit of the vertex's own (scaled) value; scaling keeps signs
 #pragma unroll
             for (int k = 0; k < VEC; k++)
                 sv[k] = (r0 + k < R) ? is_neg(A.gin[(int64_t)itm.v * R + r0 + k]) : 0u;
         }
+        // blocks of 32 neighbours (fixed order), SL column ids loaded at a time
         for (int j0 = itm.beg; j0 < itm.end; j0 += 32) {
             const int cnt = min(32, itm.end - j0);
-            const uint32_t mycol = lane < cnt ? (uint32_t)A.col[j0 + lane] : 0u;
 #pragma unroll
             for (int k = 0; k < VEC; k++) blk[k] = 0.f;
-            for (int q = 0; q < cnt; q++) {
-                const uint32_t cc = __shfl_sync(0xffffffffu, mycol, q);
-                const uint32_t nb = cc & 0x80000000u;
-                const uint32_t nb1 = cc >> 31;
-                const int64_t base = (int64_t)(cc & SB_ID_MASK) * R + r0;
-                if (act) {
-                    if (VEC == 4) {
-                        const float4 x = Vec<4>::ld(A.gin + base);
-                        blk[0] += flip_sign(x.x, nb);
-                        blk[1 % VEC] += flip_sign(x.y, nb);
-                        blk[2 % VEC] += flip_sign(x.z, nb);
-                        blk[3 % VEC] += flip_sign(x.w, nb);
-                        if (wantF) {
-                            fcnt[0] += (int)(is_neg(x.x) ^ nb1 ^ sv[0]);
-                            fcnt[1 % VEC] += (int)(is_neg(x.y) ^ nb1 ^ sv[1 % VEC]);
-                            fcnt[2 % VEC] += (int)(is_neg(x.z) ^ nb1 ^ sv[2 % VEC]);
-                            fcnt[3 % VEC] += (int)(is_neg(x.w) ^ nb1 ^ sv[3 % VEC]);
+            for (int jj = 0; jj < cnt; jj += SL) {
+                const int cc_n = min(SL, cnt - jj);
+                const uint32_t mycol = sl < cc_n ? (uint32_t)__ldg(A.col + j0 + jj + sl) : 0u;
+                for (int q = 0; q < cc_n; q++) {
+                    const uint32_t cc = __shfl_sync(smask, mycol, q, SL);
+                    const uint32_t nb = cc & 0x80000000u;
+                    const uint32_t nb1 = cc >> 31;
+                    const int64_t base = (int64_t)(cc & SB_ID_MASK) * R + r0;
+                    if (act) {
+                        if (VEC == 4) {
+                            const float4 x = Vec<4>::ld(A.gin + base);
+                            blk[0] += flip_sign(x.x, nb);
+                            blk[1 % VEC] += flip_sign(x.y, nb);
+                            blk[2 % VEC] += flip_sign(x.z, nb);
+                            blk[3 % VEC] += flip_sign(x.w, nb);
+                            if (wantF) {
+                                fcnt[0] += (int)(is_neg(x.x) ^ nb1 ^ sv[0]);
+                                fcnt[1 % VEC] += (int)(is_neg(x.y) ^ nb1 ^ sv[1 % VEC]);
+                                fcnt[2 % VEC] += (int)(is_neg(x.z) ^ nb1 ^ sv[2 % VEC]);
+                                fcnt[3 % VEC] += (int)(is_neg(x.w) ^ nb1 ^ sv[3 % VEC]);
+                            }
+                        } else {
+                            const float x = Vec<1>::ld(A.gin + base);
+                            blk[0] += flip_sign(x, nb);
+                            if (wantF) fcnt[0] += (int)(is_neg(x) ^ nb1 ^ sv[0]);
                         }
-                    } else if (r0 < R) {
-                        const float x = Vec<1>::ld(A.gin + base);
-                        blk[0] += flip_sign(x, nb);
-                        if (wantF) fcnt[0] += (int)(is_neg(x) ^ nb1 ^ sv[0]);
                     }
                 }
             }
@@ -327,7 +335,7 @@ template <bool STEP>
 static sb_status gl_rows_launch(sb_ctx* c, GlArgs& A)
 {
     const bool vec4 = (A.R % 4 == 0) && (((uintptr_t)A.gin & 15) == 0);
-    const void* fn = vec4 ? (const void*)k_gl_rows<4, STEP> : (const void*)k_gl_rows<1, STEP>;
+    const void* fn = vec4 ? (const void*)k_gl_rows<4, 8, STEP> : (const void*)k_gl_rows<1, 32, STEP>;
     size_t smem = STEP ? sizeof(uint32_t) * 2 * (size_t)A.R : 0;
     if (smem > 48 * 1024) SB_CHECK_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;

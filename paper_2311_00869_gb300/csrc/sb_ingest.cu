@@ -224,13 +224,34 @@ __global__ void k_chunks(const int32_t* __restrict__ deg, int64_t n, int chunk, 
 
 // work items: one per row chunk; split rows get an index and the position of
 // their first chunk among the chunks of split rows
+// sort key placing high-degree rows first (ties by vertex id)
+__global__ void k_degkeys(const int32_t* __restrict__ deg, int64_t n, uint64_t* __restrict__ keys)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        keys[v] = ((uint64_t)(0x7FFFFFFFu - (uint32_t)deg[v]) << 32) | (uint64_t)v;
+}
+
+__global__ void k_perm(const uint64_t* __restrict__ keys, int64_t n, const int32_t* __restrict__ nch,
+                       int32_t* __restrict__ perm, int32_t* __restrict__ nch_sorted)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v = (int32_t)(keys[i] & 0xFFFFFFFFull);
+        perm[i] = v;
+        nch_sorted[i] = nch[v];
+    }
+}
+
+// work items of row position i (vertex perm[i], or i when perm is null);
+// ipos is indexed by position
 __global__ void k_items(const int32_t* __restrict__ rowptr, int64_t n, int chunk, const int32_t* __restrict__ nch,
                         const int32_t* __restrict__ ipos, const int32_t* __restrict__ split,
                         const int32_t* __restrict__ hpos, const int32_t* __restrict__ splitpos,
-                        sb_bfs_item* __restrict__ items, int32_t* __restrict__ hub_vertex,
-                        int32_t* __restrict__ hub_first, int32_t* __restrict__ hub_count)
+                        const int32_t* __restrict__ perm, sb_bfs_item* __restrict__ items,
+                        int32_t* __restrict__ hub_vertex, int32_t* __restrict__ hub_first,
+                        int32_t* __restrict__ hub_count)
 {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = perm ? perm[i] : i;
         int32_t b = rowptr[v], e = rowptr[v + 1], c = nch[v];
         int32_t hub = split[v] ? hpos[v] : -1;
         if (hub >= 0) {
@@ -244,7 +265,7 @@ __global__ void k_items(const int32_t* __restrict__ rowptr, int64_t n, int chunk
             it.beg = b + k * chunk;
             it.end = min(e, b + (k + 1) * chunk);
             it.hub = hub;
-            items[ipos[v] + k] = it;
+            items[ipos[i] + k] = it;
         }
     }
 }
@@ -309,9 +330,9 @@ struct IngestTmp {
 
 // Builds the work items of one chunk size: returns items, split-row vertex
 // list (and optionally first partial slot / chunk count per split row).
-static sb_status build_items(sb_ctx* c, const int32_t* deg, int64_t n, int chunk, sb_bfs_item** items_out,
-                             int64_t* n_items, int32_t** hub_vertex, int64_t* n_hubs, int32_t** hub_first,
-                             int32_t** hub_count, int64_t* n_partials)
+static sb_status build_items(sb_ctx* c, const int32_t* deg, int64_t n, int chunk, bool by_degree,
+                             sb_bfs_item** items_out, int64_t* n_items, int32_t** hub_vertex, int64_t* n_hubs,
+                             int32_t** hub_first, int32_t** hub_count, int64_t* n_partials)
 {
     IngestTmp T(c);
     int32_t* nch = T.get<int32_t>(n);
@@ -325,7 +346,21 @@ static sb_status build_items(sb_ctx* c, const int32_t* deg, int64_t n, int chunk
     unsigned g = grid_for(c, n);
     k_chunks<<<g, 256, 0, c->stream>>>(deg, n, chunk, nch, split);
     SB_TRY(sb_after_launch(c, "k_chunks"));
-    SB_TRY(sb_scan_i32(c, nch, ipos, n, tot + 0));
+    int32_t* perm = nullptr;
+    if (by_degree) {
+        uint64_t* keys = T.get<uint64_t>(n);
+        perm = T.get<int32_t>(n);
+        int32_t* nch_sorted = T.get<int32_t>(n);
+        if (!keys || !perm || !nch_sorted) return sb_fail(c, SB_ERR_OOM, "item scratch");
+        k_degkeys<<<g, 256, 0, c->stream>>>(deg, n, keys);
+        SB_TRY(sb_after_launch(c, "k_degkeys"));
+        SB_TRY(sb_radix_sort_u64(c, keys, n, 64));
+        k_perm<<<g, 256, 0, c->stream>>>(keys, n, nch, perm, nch_sorted);
+        SB_TRY(sb_after_launch(c, "k_perm"));
+        SB_TRY(sb_scan_i32(c, nch_sorted, ipos, n, tot + 0));
+    } else {
+        SB_TRY(sb_scan_i32(c, nch, ipos, n, tot + 0));
+    }
     SB_TRY(sb_scan_i32(c, split, hpos, n, tot + 1));
     // chunks of split rows only (for partial-sum slots)
     SB_CHECK_CUDA(c, cudaMemcpyAsync(splitch, nch, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c->stream));
@@ -344,8 +379,8 @@ static sb_status build_items(sb_ctx* c, const int32_t* deg, int64_t n, int chunk
     if (hub_count) *hub_count = (int32_t*)sb_dalloc(c, sizeof(int32_t) * (size_t)(h_tot[1] > 0 ? h_tot[1] : 1));
     if (!*items_out || !*hub_vertex || (hub_first && !*hub_first) || (hub_count && !*hub_count))
         return sb_fail(c, SB_ERR_OOM, "work items");
-    k_items<<<g, 256, 0, c->stream>>>(c->rowptr, n, chunk, nch, ipos, split, hpos, splitpos, *items_out, *hub_vertex,
-                                      hub_first ? *hub_first : nullptr, hub_count ? *hub_count : nullptr);
+    k_items<<<g, 256, 0, c->stream>>>(c->rowptr, n, chunk, nch, ipos, split, hpos, splitpos, perm, *items_out,
+                                      *hub_vertex, hub_first ? *hub_first : nullptr, hub_count ? *hub_count : nullptr);
     return sb_after_launch(c, "k_items");
 }
 
@@ -482,10 +517,10 @@ static sb_status load_graph_impl(sb_ctx* c, int64_t n, int64_t m, const int32_t*
     SB_TRY(sb_after_launch(c, "k_vweight"));
     c->n = n1;
     c->m = m2;
-    SB_TRY(build_items(c, deg, n1, SB_BFS_CHUNK, &c->items, &c->n_items, &c->hub_vertex, &c->n_hubs, nullptr,
+    SB_TRY(build_items(c, deg, n1, SB_BFS_CHUNK, true, &c->items, &c->n_items, &c->hub_vertex, &c->n_hubs, nullptr,
                        nullptr, nullptr));
-    SB_TRY(build_items(c, deg, n1, SB_GL_CHUNK, &c->gl_items, &c->n_gl_items, &c->gl_hub_vertex, &c->n_gl_hubs,
-                       &c->gl_hub_first, &c->gl_hub_count, &c->n_gl_partials));
+    SB_TRY(build_items(c, deg, n1, SB_GL_CHUNK, false, &c->gl_items, &c->n_gl_items, &c->gl_hub_vertex,
+                       &c->n_gl_hubs, &c->gl_hub_first, &c->gl_hub_count, &c->n_gl_partials));
     SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
     c->has_graph = true;
     *n_out = n1;

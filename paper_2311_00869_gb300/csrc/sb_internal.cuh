@@ -141,6 +141,7 @@ struct sb_ctx {
     int32_t* cl_rep = nullptr;     // cl_max: batch tree that created the state in this batch, else -1
     int32_t* cl_mismatch = nullptr;// K
     int64_t cl_n_host = 0;
+    std::vector<int32_t> cl_order;  // output position -> state index (by first tree)
 
     // graphL scratch
     float* gl_partial = nullptr;   // partial row sums of split rows

@@ -128,13 +128,7 @@ def test_trees_labels_counts_small(P, sb, K):
 
 def test_split_rows_hub(P, sb):
     # vertex 0 joins 700 others (split into several chunks) plus a random mesh
-    rng = np.random.Generator(np.random.PCG64(77))
-    n = 701
-    a = np.concatenate([np.zeros(700, np.int64), rng.integers(1, n, 900)])
-    b = np.concatenate([np.arange(1, n), rng.integers(1, n, 900)])
-    keep = a != b
-    a, b = a[keep].astype(np.int32), b[keep].astype(np.int32)
-    s = np.where(rng.random(a.shape[0]) < 0.35, -1, 1).astype(np.int8)
+    n, a, b, s = _hub_graph(seed=77, n=701, extra=900, neg=0.35)
     g = load_both(sb, n, a, b, s)
     assert np.diff(g.rowptr).max() > 512
     check_batch(P, sb, g, seed=5, t0=0, K=200, parents=True)
@@ -239,13 +233,14 @@ def test_cloud_capacity_error(P, sb):
 
 # ------------------------------------------------------------------ graphL
 
-def _hub_graph(seed=31, n=900):
+def _hub_graph(seed=31, n=900, extra=None, neg=0.3):
+    """Vertex 0 joined to every other vertex, plus random distinct pairs."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    a = np.concatenate([np.zeros(n - 1, np.int64), rng.integers(1, n, 2 * n)])
-    b = np.concatenate([np.arange(1, n), rng.integers(1, n, 2 * n)])
-    keep = a != b
-    a, b = a[keep].astype(np.int32), b[keep].astype(np.int32)
-    s = np.where(rng.random(a.shape[0]) < 0.3, -1, 1).astype(np.int8)
+    extra = 2 * n if extra is None else extra
+    a = np.concatenate([np.zeros(n - 1, np.int64), rng.integers(1, n, extra)])
+    b = np.concatenate([np.arange(1, n), rng.integers(1, n, extra)])
+    a, b = synth._unique_pairs_in_order(a, b)
+    s = np.where(rng.random(a.shape[0]) < neg, -1, 1).astype(np.int8)
     return n, a, b, s
 
 
