@@ -26,6 +26,7 @@ SIGNATURES = {
     "sb_sync": (i32, [P]),
     "sb_profile": (i32, [P, ctypes.c_int]),
     "sb_profile_read": (i32, [P, P, P]),
+    "sb_stats": (i32, [P, P, i32]),
     "sb_load_graph": (i32, [P, i64, i64, P, P, P, u32, ctypes.POINTER(i64), ctypes.POINTER(i64), P]),
     "sb_graph_edges": (i32, [P, P, P, P]),
     "sb_graph_csr": (i32, [P, P, P, P]),

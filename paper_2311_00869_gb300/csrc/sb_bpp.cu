@@ -20,7 +20,7 @@
 
 #define BFS_THREADS 256
 #define BFS_THREADS_PAR 128
-#define SYNC_WORDS 16
+#define SYNC_WORDS 32
 #define BAR_LIMIT_CYCLES (4ll * 1000 * 1000 * 1000)  // ~2 s at 2 GHz
 
 struct BfsArgs {
@@ -85,16 +85,21 @@ __device__ __forceinline__ unsigned group_mask(int G)
 // time so that 8 frontier gathers are in flight per lane.
 //   HASH = false: once / twice = trees reached through >= 1 / >= 2 candidates,
 //                 labx = candidate label bits (exact where once & ~twice).
-//   HASH = true : argmin of the hashed parent key over candidates in `mask`;
-//                 once = trees seen, labx = winners' label bits, best / bestu
-//                 hold the winners' hash / id in shared memory.
+//   HASH = true : running argmin of the hashed parent key over the candidates
+//                 in `mask`: best[t] (shared, initialised to 0xFFFFFFFF by the
+//                 caller) holds the smallest hash, labb[t] / bestu[t] the
+//                 winner's label bit / id.  Keys are distinct (the hash is a
+//                 bijection in u), so `h <= best` accepts exactly the minimum.
+//                 The candidate bits of the 8 neighbours are drained as one
+//                 queue, so a warp waits for the lane with the most bits in the
+//                 tile rather than for the sum of per-neighbour maxima.
 // `cur` and `lab` are rewritten between levels by other blocks, so they are
 // read with plain (coherent) loads; the column array is read-only.
 template <bool HASH, bool PAR, int BD>
 __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint64_t* cur, const uint64_t* lab, int Wb,
                                          int Wt, int wofs, int gl, uint64_t mask, uint32_t y, const uint32_t* akey_w,
-                                         uint32_t* best, int32_t* bestu, int tid, uint64_t& once, uint64_t& twice,
-                                         uint64_t& labx)
+                                         uint32_t* best, uint8_t* labb, int32_t* bestu, int tid, uint64_t& once,
+                                         uint64_t& twice, uint64_t& labx, uint32_t& nhash)
 {
     for (int j = 0; j < len; j += 8) {
         uint32_t c[8];
@@ -106,31 +111,69 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
 #pragma unroll
         for (int k = 0; k < 8; k++)
             l[k] = f[k] ? (lab[(int64_t)(c[k] & SB_ID_MASK) * Wt + wofs] ^ ((c[k] >> 31) ? ~0ull : 0ull)) : 0ull;
+        if (!HASH) {
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
-            if (!HASH) {
+            for (int k = 0; k < 8; k++) {
                 twice |= once & f[k];
                 once |= f[k];
                 labx |= f[k] & l[k];
-            } else {
-                uint64_t b = f[k];
-                const uint32_t u = c[k] & SB_ID_MASK;
-                const uint32_t hx = u ^ y;
-                while (b) {
-                    const int t = __ffsll((long long)b) - 1;
-                    const uint64_t bit = 1ull << t;
-                    b &= b - 1;
-                    const uint32_t h = sb_fmix32(hx + akey_w[t]);
-                    if (!(once & bit) || h < best[t * BD + tid]) {
-                        once |= bit;
-                        best[t * BD + tid] = h;
-                        labx = (labx & ~bit) | (l[k] & bit);
-                        if (PAR) bestu[t * BD + tid] = (int32_t)u;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                once |= f[k];
+                nhash += __popcll(f[k]);
+            }
+            // drain the tile's candidate bits as one queue (head = f[0])
+            int rem = 8;
+            while (rem > 0) {
+                if (f[0] == 0) {
+#pragma unroll
+                    for (int k = 0; k < 7; k++) {
+                        f[k] = f[k + 1];
+                        l[k] = l[k + 1];
+                        c[k] = c[k + 1];
                     }
+                    f[7] = 0;
+                    rem--;
+                    continue;
+                }
+                const int t = __ffsll((long long)f[0]) - 1;
+                f[0] &= f[0] - 1;
+                const uint32_t u = c[0] & SB_ID_MASK;
+                const uint32_t h = sb_fmix32((u ^ y) + akey_w[t]);
+                if (h <= best[t * BD + tid]) {
+                    best[t * BD + tid] = h;
+                    labb[t * BD + tid] = (uint8_t)((l[0] >> t) & 1ull);
+                    if (PAR) bestu[t * BD + tid] = (int32_t)u;
                 }
             }
         }
     }
+}
+
+// Resets the running minima of the trees in `mask` and, after a hash pass,
+// collects the winners' label bits.
+template <int BD>
+__device__ __forceinline__ void best_reset(uint32_t* best, int tid, uint64_t mask)
+{
+    for (uint64_t b = mask; b;) {
+        const int t = __ffsll((long long)b) - 1;
+        b &= b - 1;
+        best[t * BD + tid] = 0xFFFFFFFFu;
+    }
+}
+
+template <int BD>
+__device__ __forceinline__ uint64_t winner_labels(const uint8_t* labb, int tid, uint64_t mask)
+{
+    uint64_t lx = 0;
+    for (uint64_t b = mask; b;) {
+        const int t = __ffsll((long long)b) - 1;
+        b &= b - 1;
+        lx |= (uint64_t)labb[t * BD + tid] << t;
+    }
+    return lx;
 }
 
 template <int G, bool PAR>
@@ -141,7 +184,8 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
     extern __shared__ uint32_t smem[];
     uint32_t* akey = smem;                        // Wb * 64 tree salts
     uint32_t* best = smem + SB_WORDS_MAX * 64;    // 64 x BD running minima
-    int32_t* bestu = (int32_t*)(best + 64 * BD);  // 64 x BD winners (PAR only)
+    uint8_t* labb = (uint8_t*)(best + 64 * BD);   // 64 x BD winners' label bits
+    int32_t* bestu = (int32_t*)(labb + 64 * BD);  // 64 x BD winners (PAR only)
     __shared__ uint32_t s_any;
 
     const int tid = threadIdx.x;
@@ -159,6 +203,7 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
     const int Wb = A.Wb, Wt = A.Wt, w0 = A.w0;
     const int wofs = w0 + gl;
     const uint32_t* akey_w = akey + gl * 64;
+    uint32_t n_scan = 0, n_hash = 0, n_pass2 = 0;  // work counters
     int L = 1;
     while (true) {
         const uint64_t* cur = (L & 1) ? A.fr0 : A.fr1;
@@ -179,19 +224,24 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
             uint64_t once = 0, twice = 0, labx = 0;
             if (U) {
                 const uint32_t y = sb_child_salt(A.S, (uint32_t)v);
+                n_scan += (uint32_t)len;
                 if (!hub && !PAR) {
-                    scan_row<false, PAR, BD>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, akey_w, best, bestu, tid,
-                                             once, twice, labx);
+                    scan_row<false, PAR, BD>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, akey_w, best, labb, bestu,
+                                             tid, once, twice, labx, n_hash);
                     if (twice) {
                         // trees reached through two or more candidates: hashed argmin
                         uint64_t o2 = 0, t2 = 0, l2 = 0;
-                        scan_row<true, PAR, BD>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, twice, y, akey_w, best, bestu,
-                                                tid, o2, t2, l2);
-                        labx = (labx & ~twice) | (l2 & twice);
+                        n_pass2 += (uint32_t)len;
+                        best_reset<BD>(best, tid, twice);
+                        scan_row<true, PAR, BD>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, twice, y, akey_w, best, labb,
+                                                bestu, tid, o2, t2, l2, n_hash);
+                        labx = (labx & ~twice) | (winner_labels<BD>(labb, tid, twice) & twice);
                     }
                 } else {
-                    scan_row<true, PAR, BD>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, akey_w, best, bestu, tid,
-                                            once, twice, labx);
+                    best_reset<BD>(best, tid, U);
+                    scan_row<true, PAR, BD>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, akey_w, best, labb, bestu,
+                                            tid, once, twice, labx, n_hash);
+                    labx = winner_labels<BD>(labb, tid, once);
                 }
             }
             if (hub) {
@@ -289,6 +339,17 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
         __syncthreads();
     }
     if (tid == 0 && blockIdx.x == 0) A.sync[7] = (uint32_t)L;
+    // work counters (one atomic per warp and counter)
+    for (int d = 16; d; d >>= 1) {
+        n_scan += __shfl_xor_sync(0xffffffffu, n_scan, d);
+        n_hash += __shfl_xor_sync(0xffffffffu, n_hash, d);
+        n_pass2 += __shfl_xor_sync(0xffffffffu, n_pass2, d);
+    }
+    if ((tid & 31) == 0) {
+        atomicAdd((unsigned long long*)(A.sync + 8), (unsigned long long)n_scan);
+        atomicAdd((unsigned long long*)(A.sync + 10), (unsigned long long)n_hash);
+        atomicAdd((unsigned long long*)(A.sync + 12), (unsigned long long)n_pass2);
+    }
 }
 
 // ------------------------------------------------------------ BFS set-up
@@ -458,6 +519,17 @@ __global__ void __launch_bounds__(SC_THREADS) k_score(const int2* __restrict__ e
         if (scnt[i]) atomicAdd(counts + 64 * w0 + i, scnt[i]);
 }
 
+// per-launch counters are folded into the context after each launch
+__global__ void k_fold_stats(const uint32_t* sync, unsigned long long* acc)
+{
+    const unsigned long long L = sync[7];
+    if (L > acc[0]) acc[0] = L;
+    acc[1] += 1;
+    acc[2] += *(const unsigned long long*)(sync + 8);
+    acc[3] += *(const unsigned long long*)(sync + 10);
+    acc[4] += *(const unsigned long long*)(sync + 12);
+}
+
 // --------------------------------------------------------------- host side
 static int group_for(int Wb)
 {
@@ -506,7 +578,7 @@ static sb_status run_bfs(sb_ctx* c, int w0, int Wb, int32_t* parents)
     const int G = group_for(Wb);
     const int BD = par ? BFS_THREADS_PAR : BFS_THREADS;
     const void* fn = par ? bfs_kernel<true>(G) : bfs_kernel<false>(G);
-    size_t smem = sizeof(uint32_t) * (SB_WORDS_MAX * 64 + 64 * BD) + (par ? sizeof(int32_t) * 64 * BD : 0);
+    size_t smem = sizeof(uint32_t) * (SB_WORDS_MAX * 64 + 64 * BD) + 64 * BD + (par ? sizeof(int32_t) * 64 * BD : 0);
     SB_CHECK_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     SB_CHECK_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BD, smem));
@@ -524,7 +596,7 @@ static sb_status run_bfs(sb_ctx* c, int w0, int Wb, int32_t* parents)
     k_bfs_roots<<<(unsigned)sb_cdiv(64 * Wb, 256), 256, 0, c->stream>>>(n, Wb, w0, c->K, sb_seed_key(c->seed),
                                                                         c->tree_begin, c->vis, c->fr0, parents);
     SB_TRY(sb_after_launch(c, "k_bfs_roots"));
-    SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync, 0, sizeof(uint32_t) * SYNC_WORDS, c->stream));
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync, 0, sizeof(uint32_t) * 16, c->stream));
     BfsArgs A;
     A.items = c->items;
     A.n_items = c->n_items;
@@ -547,9 +619,13 @@ static sb_status run_bfs(sb_ctx* c, int w0, int Wb, int32_t* parents)
     A.S = sb_seed_key(c->seed);
     A.tree0 = c->tree_begin;
     void* args[] = {&A};
-    SbProf prof(c, SB_PROF_BFS);
-    SB_CHECK_CUDA(c, cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(BD), args, smem, c->stream));
-    return sb_after_launch(c, "k_bfs");
+    {
+        SbProf prof(c, SB_PROF_BFS);
+        SB_CHECK_CUDA(c, cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(BD), args, smem, c->stream));
+        SB_TRY(sb_after_launch(c, "k_bfs"));
+    }
+    k_fold_stats<<<1, 1, 0, c->stream>>>(c->sync, (unsigned long long*)(c->sync + 16));
+    return sb_after_launch(c, "k_fold_stats");
 }
 
 static sb_status check_sync_error(sb_ctx* c)
@@ -615,6 +691,7 @@ extern "C" sb_status sb_sample_trees(sb_ctx* c, uint64_t seed, int64_t tree_begi
     c->has_batch = false;
     c->counts_valid = false;
     c->batch_in_cloud = false;
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync + 16, 0, sizeof(uint32_t) * 16, c->stream));
     for (int w0 = 0; w0 < W; w0 += SB_WORDS_MAX) {
         int Wb = W - w0 < SB_WORDS_MAX ? W - w0 : SB_WORDS_MAX;
         SB_TRY(run_bfs(c, w0, Wb, parents_out));
@@ -693,4 +770,19 @@ extern "C" sb_status sb_label(sb_ctx* c, uint64_t* labels_out)
     cudaStreamSynchronize(c->stream);
     sb_dfree(c, tmp);
     return st;
+}
+
+extern "C" sb_status sb_stats(sb_ctx* c, int64_t* out, int32_t n)
+{
+    if (!c || !out || n < 0 || n > SB_STATS_N) return SB_ERR_ARG;
+    if (!c->sync) {
+        for (int i = 0; i < n; i++) out[i] = 0;
+        return SB_OK;
+    }
+    SB_CHECK_CUDA(c, cudaSetDevice(c->device));
+    unsigned long long acc[8];
+    SB_CHECK_CUDA(c, cudaMemcpyAsync(acc, c->sync + 16, sizeof(acc), cudaMemcpyDeviceToHost, c->stream));
+    SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < n; i++) out[i] = (int64_t)acc[i];
+    return SB_OK;
 }

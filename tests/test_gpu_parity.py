@@ -284,7 +284,7 @@ def test_graphl_autograd_function(P, sb):
 def test_graphl_descent_and_round(P, sb):
     n, a, b, s = _hub_graph(seed=9, n=600)
     g = load_both(sb, n, a, b, s)
-    R, steps, alpha = 8, 40, 0.05
+    R, steps, alpha = 8, 90, 0.05
     gam = synth.gamma0(g.n, R, seed=2)
     G0 = torch.from_numpy(gam).cuda()
     out, exps, F_trace, F_final = sb.graphL_descent(G0, alpha, steps, renorm_log2=32, trace=True)
