@@ -103,9 +103,10 @@ sb_status sb_profile_read(sb_ctx* ctx, double* ms_out, int64_t* launches_out);
 /* Work counters of the last sb_sample_trees call (host array, n entries,
    n <= SB_STATS_N): [0] BFS levels (largest over its launches), [1] BFS
    launches, [2] neighbour entries scanned (per vertex-word lane),
-   [3] hashed parent candidates, [4] second-pass entries (trees with two or
-   more candidates).  Synchronises the stream. */
-#define SB_STATS_N 5
+   [3] hashed parent candidates of whole rows, [4] second-pass entries
+   (trees with two or more candidates), [5] hashed parent candidates of split
+   rows.  Synchronises the stream. */
+#define SB_STATS_N 6
 sb_status sb_stats(sb_ctx* ctx, int64_t* out, int32_t n);
 
 /* ------------------------------------------------------------ graph ingest */

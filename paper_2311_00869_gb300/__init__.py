@@ -218,10 +218,11 @@ class SignedBal:
 
     def stats(self):
         """Work counters of the last sample_trees call."""
-        out = np.zeros(5, np.int64)
-        self._check(self.lib.sb_stats(self.h, _ptr(out), 5))
+        out = np.zeros(6, np.int64)
+        self._check(self.lib.sb_stats(self.h, _ptr(out), 6))
         return {"bfs_levels": int(out[0]), "bfs_launches": int(out[1]), "scan_entries": int(out[2]),
-                "hashed_candidates": int(out[3]), "second_pass_entries": int(out[4])}
+                "hashed_candidates": int(out[3]), "second_pass_entries": int(out[4]),
+                "hashed_candidates_split_rows": int(out[5])}
 
     PROF_FAMILIES = ("bfs", "score", "hash", "cloud", "ingest", "gl_rows", "gl_fwd", "other")
 

@@ -18,7 +18,7 @@
 
 #include "sb_internal.cuh"
 
-#define BFS_THREADS 256
+#define BFS_THREADS 128
 #define BFS_THREADS_PAR 128
 #define SYNC_WORDS 32
 #define BAR_LIMIT_CYCLES (4ll * 1000 * 1000 * 1000)  // ~2 s at 2 GHz
@@ -81,25 +81,43 @@ __device__ __forceinline__ unsigned group_mask(int G)
     return ((1u << G) - 1u) << base;
 }
 
-// One pass over a CSR range for one (vertex, word) lane, 8 neighbours at a
-// time so that 8 frontier gathers are in flight per lane.
+// Group-wide exclusive prefix sum over the G lanes of one vertex.
+template <int G>
+__device__ __forceinline__ int group_excl_scan(int x, unsigned gmask, int gl, int& total)
+{
+    int incl = x;
+#pragma unroll
+    for (int d = 1; d < G; d <<= 1) {
+        const int y = __shfl_up_sync(gmask, incl, d, G);
+        if (gl >= d) incl += y;
+    }
+    total = __shfl_sync(gmask, incl, G - 1, G);
+    return incl - x;
+}
+
+// One pass over a CSR range for one vertex: lane gl of the group owns word
+// w0 + gl.  Neighbours are read 8 at a time so that 8 frontier gathers are in
+// flight per lane.
 //   HASH = false: once / twice = trees reached through >= 1 / >= 2 candidates,
 //                 labx = candidate label bits (exact where once & ~twice).
 //   HASH = true : running argmin of the hashed parent key over the candidates
-//                 in `mask`: best[t] (shared, initialised to 0xFFFFFFFF by the
-//                 caller) holds the smallest hash, labb[t] / bestu[t] the
-//                 winner's label bit / id.  Keys are distinct (the hash is a
-//                 bijection in u), so `h <= best` accepts exactly the minimum.
-//                 The candidate bits of the 8 neighbours are drained as one
-//                 queue, so a warp waits for the lane with the most bits in the
-//                 tile rather than for the sum of per-neighbour maxima.
+//                 in `mask`.  For each neighbour the group's candidate bits are
+//                 first compacted into a shared queue (entry = owner lane,
+//                 tree, label bit), then hashed by all lanes of the group in
+//                 lockstep; a neighbour contributes at most one entry per
+//                 (word, tree), so the slot updates of one round never collide.
+//                 best[slot] (initialised to 0xFFFFFFFF) holds the smallest
+//                 hash, labb / bestu the winner's label bit / id; keys are
+//                 distinct (the hash is a bijection in u), so `h <= best`
+//                 accepts exactly the minimum.  `once` returns the trees seen.
 // `cur` and `lab` are rewritten between levels by other blocks, so they are
 // read with plain (coherent) loads; the column array is read-only.
-template <bool HASH, bool PAR, int BD>
+template <bool HASH, bool PAR, int BD, int G>
 __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint64_t* cur, const uint64_t* lab, int Wb,
-                                         int Wt, int wofs, int gl, uint64_t mask, uint32_t y, const uint32_t* akey_w,
-                                         uint32_t* best, uint8_t* labb, int32_t* bestu, int tid, uint64_t& once,
-                                         uint64_t& twice, uint64_t& labx, uint32_t& nhash)
+                                         int Wt, int wofs, int gl, uint64_t mask, uint32_t y, const uint32_t* akey,
+                                         uint32_t* best, uint8_t* labb, int32_t* bestu, uint16_t* queue, int tid,
+                                         unsigned gmask, uint64_t& once, uint64_t& twice, uint64_t& labx,
+                                         uint32_t& nhash)
 {
     for (int j = 0; j < len; j += 8) {
         uint32_t c[8];
@@ -119,34 +137,35 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
                 labx |= f[k] & l[k];
             }
         } else {
+            const int owner0 = tid - gl;  // thread index of the group's lane 0
 #pragma unroll
             for (int k = 0; k < 8; k++) {
                 once |= f[k];
-                nhash += __popcll(f[k]);
-            }
-            // drain the tile's candidate bits as one queue (head = f[0])
-            int rem = 8;
-            while (rem > 0) {
-                if (f[0] == 0) {
-#pragma unroll
-                    for (int k = 0; k < 7; k++) {
-                        f[k] = f[k + 1];
-                        l[k] = l[k + 1];
-                        c[k] = c[k + 1];
+                const int cnt = __popcll(f[k]);
+                int T;
+                int pos = group_excl_scan<G>(cnt, gmask, gl, T);
+                if (T == 0) continue;  // same for the whole group
+                nhash += (uint32_t)cnt;
+                for (uint64_t b = f[k]; b;) {
+                    const int t = __ffsll((long long)b) - 1;
+                    b &= b - 1;
+                    queue[pos++] = (uint16_t)((gl << 7) | (t << 1) | (int)((l[k] >> t) & 1ull));
+                }
+                __syncwarp(gmask);
+                const uint32_t u = c[k] & SB_ID_MASK;
+                const uint32_t hx = u ^ y;
+                for (int i = gl; i < T; i += G) {
+                    const uint32_t e = queue[i];
+                    const int ow = (int)(e >> 7), t = (int)((e >> 1) & 63u);
+                    const uint32_t h = sb_fmix32(hx + akey[ow * 64 + t]);
+                    const int slot = t * BD + owner0 + ow;
+                    if (h <= best[slot]) {
+                        best[slot] = h;
+                        labb[slot] = (uint8_t)(e & 1u);
+                        if (PAR) bestu[slot] = (int32_t)u;
                     }
-                    f[7] = 0;
-                    rem--;
-                    continue;
                 }
-                const int t = __ffsll((long long)f[0]) - 1;
-                f[0] &= f[0] - 1;
-                const uint32_t u = c[0] & SB_ID_MASK;
-                const uint32_t h = sb_fmix32((u ^ y) + akey_w[t]);
-                if (h <= best[t * BD + tid]) {
-                    best[t * BD + tid] = h;
-                    labb[t * BD + tid] = (uint8_t)((l[0] >> t) & 1ull);
-                    if (PAR) bestu[t * BD + tid] = (int32_t)u;
-                }
+                __syncwarp(gmask);
             }
         }
     }
@@ -185,7 +204,8 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
     uint32_t* akey = smem;                        // Wb * 64 tree salts
     uint32_t* best = smem + SB_WORDS_MAX * 64;    // 64 x BD running minima
     uint8_t* labb = (uint8_t*)(best + 64 * BD);   // 64 x BD winners' label bits
-    int32_t* bestu = (int32_t*)(labb + 64 * BD);  // 64 x BD winners (PAR only)
+    uint16_t* queues = (uint16_t*)(labb + 64 * BD);  // 64 x G entries per group
+    int32_t* bestu = (int32_t*)(queues + 64 * BD);   // 64 x BD winners (PAR only)
     __shared__ uint32_t s_any;
 
     const int tid = threadIdx.x;
@@ -202,8 +222,8 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
 
     const int Wb = A.Wb, Wt = A.Wt, w0 = A.w0;
     const int wofs = w0 + gl;
-    const uint32_t* akey_w = akey + gl * 64;
-    uint32_t n_scan = 0, n_hash = 0, n_pass2 = 0;  // work counters
+    uint16_t* queue = queues + (tid / G) * (64 * G);
+    uint32_t n_scan = 0, n_hash = 0, n_pass2 = 0, n_hash_hub = 0;  // work counters
     int L = 1;
     while (true) {
         const uint64_t* cur = (L & 1) ? A.fr0 : A.fr1;
@@ -226,21 +246,21 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
                 const uint32_t y = sb_child_salt(A.S, (uint32_t)v);
                 n_scan += (uint32_t)len;
                 if (!hub && !PAR) {
-                    scan_row<false, PAR, BD>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, akey_w, best, labb, bestu,
-                                             tid, once, twice, labx, n_hash);
+                    scan_row<false, PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, akey, best, labb, bestu,
+                                                queue, tid, gmask, once, twice, labx, n_hash);
                     if (twice) {
                         // trees reached through two or more candidates: hashed argmin
                         uint64_t o2 = 0, t2 = 0, l2 = 0;
                         n_pass2 += (uint32_t)len;
                         best_reset<BD>(best, tid, twice);
-                        scan_row<true, PAR, BD>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, twice, y, akey_w, best, labb,
-                                                bestu, tid, o2, t2, l2, n_hash);
+                        scan_row<true, PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, twice, y, akey, best, labb,
+                                                   bestu, queue, tid, gmask, o2, t2, l2, n_hash);
                         labx = (labx & ~twice) | (winner_labels<BD>(labb, tid, twice) & twice);
                     }
                 } else {
                     best_reset<BD>(best, tid, U);
-                    scan_row<true, PAR, BD>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, akey_w, best, labb, bestu,
-                                            tid, once, twice, labx, n_hash);
+                    scan_row<true, PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, akey, best, labb, bestu,
+                                               queue, tid, gmask, once, twice, labx, hub ? n_hash_hub : n_hash);
                     labx = winner_labels<BD>(labb, tid, once);
                 }
             }
@@ -344,11 +364,13 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
         n_scan += __shfl_xor_sync(0xffffffffu, n_scan, d);
         n_hash += __shfl_xor_sync(0xffffffffu, n_hash, d);
         n_pass2 += __shfl_xor_sync(0xffffffffu, n_pass2, d);
+        n_hash_hub += __shfl_xor_sync(0xffffffffu, n_hash_hub, d);
     }
     if ((tid & 31) == 0) {
         atomicAdd((unsigned long long*)(A.sync + 8), (unsigned long long)n_scan);
         atomicAdd((unsigned long long*)(A.sync + 10), (unsigned long long)n_hash);
         atomicAdd((unsigned long long*)(A.sync + 12), (unsigned long long)n_pass2);
+        atomicAdd((unsigned long long*)(A.sync + 14), (unsigned long long)n_hash_hub);
     }
 }
 
@@ -528,6 +550,7 @@ __global__ void k_fold_stats(const uint32_t* sync, unsigned long long* acc)
     acc[2] += *(const unsigned long long*)(sync + 8);
     acc[3] += *(const unsigned long long*)(sync + 10);
     acc[4] += *(const unsigned long long*)(sync + 12);
+    acc[5] += *(const unsigned long long*)(sync + 14);
 }
 
 // --------------------------------------------------------------- host side
@@ -578,7 +601,8 @@ static sb_status run_bfs(sb_ctx* c, int w0, int Wb, int32_t* parents)
     const int G = group_for(Wb);
     const int BD = par ? BFS_THREADS_PAR : BFS_THREADS;
     const void* fn = par ? bfs_kernel<true>(G) : bfs_kernel<false>(G);
-    size_t smem = sizeof(uint32_t) * (SB_WORDS_MAX * 64 + 64 * BD) + 64 * BD + (par ? sizeof(int32_t) * 64 * BD : 0);
+    size_t smem = sizeof(uint32_t) * (SB_WORDS_MAX * 64 + 64 * BD) + 64 * BD + sizeof(uint16_t) * 64 * BD +
+                  (par ? sizeof(int32_t) * 64 * BD : 0);
     SB_CHECK_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     SB_CHECK_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BD, smem));

@@ -117,37 +117,28 @@ __global__ void __launch_bounds__(GL_THREADS) k_gl_rows(GlArgs A)
             for (int jj = 0; jj < cnt; jj += SL) {
                 const int cc_n = min(SL, cnt - jj);
                 const uint32_t mycol = sl < cc_n ? (uint32_t)__ldg(A.col + j0 + jj + sl) : 0u;
-                // issue the SL row gathers first, then add them in neighbour order
-                uint32_t cq[SL];
-                typename Vec<VEC>::T xq[SL];
-#pragma unroll
-                for (int q = 0; q < SL; q++) {
-                    cq[q] = __shfl_sync(smask, mycol, q, SL);
-                    if (act && q < cc_n) xq[q] = Vec<VEC>::ld(A.gin + (int64_t)(cq[q] & SB_ID_MASK) * R + r0);
-                }
-                if (act) {
-#pragma unroll
-                    for (int q = 0; q < SL; q++) {
-                        if (q < cc_n) {
-                            const uint32_t nb = cq[q] & 0x80000000u;
-                            const uint32_t nb1 = cq[q] >> 31;
-                            if constexpr (VEC == 4) {
-                                const float4 x = xq[q];
-                                blk[0] += flip_sign(x.x, nb);
-                                blk[1 % VEC] += flip_sign(x.y, nb);
-                                blk[2 % VEC] += flip_sign(x.z, nb);
-                                blk[3 % VEC] += flip_sign(x.w, nb);
-                                if (wantF) {
-                                    fcnt[0] += (int)(is_neg(x.x) ^ nb1 ^ sv[0]);
-                                    fcnt[1 % VEC] += (int)(is_neg(x.y) ^ nb1 ^ sv[1 % VEC]);
-                                    fcnt[2 % VEC] += (int)(is_neg(x.z) ^ nb1 ^ sv[2 % VEC]);
-                                    fcnt[3 % VEC] += (int)(is_neg(x.w) ^ nb1 ^ sv[3 % VEC]);
-                                }
-                            } else {
-                                const float x = xq[q];
-                                blk[0] += flip_sign(x, nb);
-                                if (wantF) fcnt[0] += (int)(is_neg(x) ^ nb1 ^ sv[0]);
+                for (int q = 0; q < cc_n; q++) {
+                    const uint32_t cc = __shfl_sync(smask, mycol, q, SL);
+                    const uint32_t nb = cc & 0x80000000u;
+                    const uint32_t nb1 = cc >> 31;
+                    const int64_t base = (int64_t)(cc & SB_ID_MASK) * R + r0;
+                    if (act) {
+                        if (VEC == 4) {
+                            const float4 x = Vec<4>::ld(A.gin + base);
+                            blk[0] += flip_sign(x.x, nb);
+                            blk[1 % VEC] += flip_sign(x.y, nb);
+                            blk[2 % VEC] += flip_sign(x.z, nb);
+                            blk[3 % VEC] += flip_sign(x.w, nb);
+                            if (wantF) {
+                                fcnt[0] += (int)(is_neg(x.x) ^ nb1 ^ sv[0]);
+                                fcnt[1 % VEC] += (int)(is_neg(x.y) ^ nb1 ^ sv[1 % VEC]);
+                                fcnt[2 % VEC] += (int)(is_neg(x.z) ^ nb1 ^ sv[2 % VEC]);
+                                fcnt[3 % VEC] += (int)(is_neg(x.w) ^ nb1 ^ sv[3 % VEC]);
                             }
+                        } else {
+                            const float x = Vec<1>::ld(A.gin + base);
+                            blk[0] += flip_sign(x, nb);
+                            if (wantF) fcnt[0] += (int)(is_neg(x) ^ nb1 ^ sv[0]);
                         }
                     }
                 }
