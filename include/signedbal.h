@@ -137,6 +137,38 @@ sb_status sb_graph_edges(sb_ctx* ctx, int32_t* u_out, int32_t* v_out, int8_t* ne
    2m entries.  Host or device, nullable. */
 sb_status sb_graph_csr(sb_ctx* ctx, int32_t* rowptr_out, int32_t* col_out, int8_t* neg_out);
 
+/*
+ * Loads a batch of G signed graphs as one disjoint union, to run thousands of
+ * small uneven graphs through the same launches (each sb_* call then works on
+ * every graph at once).  Graph g has nv[g] vertices with local ids
+ * [0, nv[g]) and the input edges [eofs[g], eofs[g+1]) of src / dst / sign
+ * (host or device, local ids).  Each graph is cleaned on its own exactly as
+ * sb_load_graph cleans one graph (with SB_LOAD_LCC: its own largest
+ * component); errors name the first offending edge of the whole input.
+ * nv, eofs: host, G and G+1 entries (eofs[0] = 0).  Outputs (host, G entries,
+ * nullable): vertices and edges of each cleaned graph.  Cleaned graph g holds
+ * the union's vertices [sum of earlier nv_out, ...) in order.
+ * In a batch, sb_sample_trees(seed, t0, K) samples K trees in EVERY graph:
+ * tree t of graph g is exactly tree t of sb_load_graph(graph g) with the
+ * same seed (ids are taken inside each graph).  sb_frustration then returns
+ * G x K counts / hashes (graph-major), and sb_label canonicalises each graph
+ * by its own vertex 0.  sb_graphL_* treat the union as one graph (the graphs
+ * share no edge, so the loss and gradient are per-graph sums).  sb_cloud is
+ * not available on a batch: use sb_batch_cloud.
+ */
+sb_status sb_load_batch(sb_ctx* ctx, int64_t n_graphs, const int64_t* nv, const int64_t* eofs, const int32_t* src,
+                        const int32_t* dst, const int8_t* sign, uint32_t flags, int64_t* nv_out, int64_t* m_out);
+
+/*
+ * Frustration cloud of every graph of a batch for the trees of the last
+ * sb_sample_trees (K <= 1024): the distinct states of each graph's K trees,
+ * checked bit for bit on every hash match (Alg. 1 lines 8-14).  Host or
+ * device outputs: n_states_out[G], fr_min_out[G] (= min S, Eq. 1), and
+ * entries_out[G x K] (nullable): graph g's states at [g*K, g*K + n_states[g])
+ * in order of first appearance.
+ */
+sb_status sb_batch_cloud(sb_ctx* ctx, int32_t* n_states_out, int32_t* fr_min_out, sb_cloud_entry* entries_out);
+
 /* ---------------------------------------------------------------- graphBpp */
 
 /*

@@ -111,6 +111,45 @@ class SignedBal:
         self.n, self.m = n_out.value, m_out.value
         return self.n, self.m, vmap
 
+    def load_batch(self, graphs, flags=LOAD_LCC | LOAD_MERGE_DUP):
+        """graphs: list of (n, src, dst, sign) with local ids.  Returns the
+        cleaned (n_g, m_g) arrays."""
+        G = len(graphs)
+        nv = np.array([g[0] for g in graphs], np.int64)
+        eofs = np.zeros(G + 1, np.int64)
+        eofs[1:] = np.cumsum([len(g[1]) for g in graphs])
+        src = np.ascontiguousarray(np.concatenate([np.asarray(g[1], np.int32) for g in graphs]))
+        dst = np.ascontiguousarray(np.concatenate([np.asarray(g[2], np.int32) for g in graphs]))
+        sign = np.ascontiguousarray(np.concatenate([np.asarray(g[3], np.int8) for g in graphs]))
+        nv_out = np.zeros(G, np.int64)
+        m_out = np.zeros(G, np.int64)
+        self._check(self.lib.sb_load_batch(self.h, G, _ptr(nv), _ptr(eofs), _ptr(src), _ptr(dst), _ptr(sign), flags,
+                                           _ptr(nv_out), _ptr(m_out)))
+        self.batch_G = G
+        self.n, self.m = int(nv_out.sum()), int(m_out.sum())
+        return nv_out, m_out
+
+    def batch_frustration(self):
+        """(G, K) counts and hashes of the last sample in a batch."""
+        counts = torch.empty((self.batch_G, self.K), dtype=torch.int32, device=self.device)
+        hashes = torch.empty((self.batch_G, self.K), dtype=torch.int64, device=self.device)
+        self._check(self.lib.sb_frustration(self.h, _ptr(counts), _ptr(hashes)))
+        return counts, hashes
+
+    def batch_cloud(self, want_entries=True):
+        G, K = self.batch_G, self.K
+        ns = np.zeros(G, np.int32)
+        fm = np.zeros(G, np.int32)
+        ent = (_abi.CloudEntry * (G * K))() if want_entries else None
+        self._check(self.lib.sb_batch_cloud(self.h, _ptr(ns), _ptr(fm),
+                                            ctypes.cast(ent, ctypes.c_void_p) if want_entries else None))
+        out = {"n_states": ns, "fr_min": fm}
+        if want_entries:
+            arr = np.ctypeslib.as_array(ent).reshape(G, K)
+            out["entries"] = [{k: np.array(arr[g, : ns[g]][k]) for k in ("hash", "S", "count", "first_tree")}
+                              for g in range(G)]
+        return out
+
     def graph_edges(self):
         u = torch.empty(self.m, dtype=torch.int32, device=self.device)
         v = torch.empty_like(u)

@@ -42,6 +42,7 @@ struct BfsArgs {
     int64_t n;
     uint64_t S;         // seed key
     int64_t tree0;      // global index of batch tree 0
+    const int32_t* vgoff;  // first vertex of each vertex's graph (batches), or null
 };
 
 // ----------------------------------------------------------- grid barrier
@@ -114,10 +115,10 @@ __device__ __forceinline__ int group_excl_scan(int x, unsigned gmask, int gl, in
 // read with plain (coherent) loads; the column array is read-only.
 template <bool HASH, bool PAR, int BD, int G>
 __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint64_t* cur, const uint64_t* lab, int Wb,
-                                         int Wt, int wofs, int gl, uint64_t mask, uint32_t y, const uint32_t* akey,
-                                         uint32_t* best, uint8_t* labb, int32_t* bestu, uint16_t* queue, int tid,
-                                         unsigned gmask, uint64_t& once, uint64_t& twice, uint64_t& labx,
-                                         uint32_t& nhash)
+                                         int Wt, int wofs, int gl, uint64_t mask, uint32_t y, uint32_t goff,
+                                         const uint32_t* akey, uint32_t* best, uint8_t* labb, int32_t* bestu,
+                                         uint16_t* queue, int tid, unsigned gmask, uint64_t& once, uint64_t& twice,
+                                         uint64_t& labx, uint32_t& nhash)
 {
     for (int j = 0; j < len; j += 8) {
         uint32_t c[8];
@@ -125,7 +126,8 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
 #pragma unroll
         for (int k = 0; k < 8; k++) c[k] = (j + k < len) ? (uint32_t)__ldg(cp + j + k) : 0u;
 #pragma unroll
-        for (int k = 0; k < 8; k++) f[k] = (j + k < len) ? (cur[(int64_t)(c[k] & SB_ID_MASK) * Wb + gl] & mask) : 0ull;
+        for (int k = 0; k < 8; k++)
+            f[k] = (j + k < len && mask) ? (cur[(int64_t)(c[k] & SB_ID_MASK) * Wb + gl] & mask) : 0ull;
 #pragma unroll
         for (int k = 0; k < 8; k++)
             l[k] = f[k] ? (lab[(int64_t)(c[k] & SB_ID_MASK) * Wt + wofs] ^ ((c[k] >> 31) ? ~0ull : 0ull)) : 0ull;
@@ -152,7 +154,7 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
                     queue[pos++] = (uint16_t)((gl << 7) | (t << 1) | (int)((l[k] >> t) & 1ull));
                 }
                 __syncwarp(gmask);
-                const uint32_t u = c[k] & SB_ID_MASK;
+                const uint32_t u = (c[k] & SB_ID_MASK) - goff;  // id inside the graph
                 const uint32_t hx = u ^ y;
                 for (int i = gl; i < T; i += G) {
                     const uint32_t e = queue[i];
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
     uint8_t* labb = (uint8_t*)(best + 64 * BD);   // 64 x BD winners' label bits
     uint16_t* queues = (uint16_t*)(labb + 64 * BD);  // 64 x G entries per group
     int32_t* bestu = (int32_t*)(queues + 64 * BD);   // 64 x BD winners (PAR only)
-    __shared__ uint32_t s_any;
+    __shared__ uint32_t s_any, s_stop;
 
     const int tid = threadIdx.x;
     const int gl = tid & (G - 1);
@@ -242,25 +244,29 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
             const int len = itm.end - itm.beg;
             const bool hub = itm.hub >= 0;
             uint64_t once = 0, twice = 0, labx = 0;
-            if (U) {
-                const uint32_t y = sb_child_salt(A.S, (uint32_t)v);
-                n_scan += (uint32_t)len;
+            // the passes below synchronise the group's lanes, so every lane of
+            // the group enters them (a lane with nothing to do has mask 0)
+            if (__any_sync(gmask, U != 0)) {
+                const uint32_t goff = A.vgoff ? (uint32_t)A.vgoff[v] : 0u;
+                const uint32_t y = sb_child_salt(A.S, (uint32_t)v - goff);
+                if (U) n_scan += (uint32_t)len;
                 if (!hub && !PAR) {
-                    scan_row<false, PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, akey, best, labb, bestu,
-                                                queue, tid, gmask, once, twice, labx, n_hash);
-                    if (twice) {
+                    scan_row<false, PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, goff, akey, best, labb,
+                                                bestu, queue, tid, gmask, once, twice, labx, n_hash);
+                    if (__any_sync(gmask, twice != 0)) {
                         // trees reached through two or more candidates: hashed argmin
                         uint64_t o2 = 0, t2 = 0, l2 = 0;
-                        n_pass2 += (uint32_t)len;
+                        if (twice) n_pass2 += (uint32_t)len;
                         best_reset<BD>(best, tid, twice);
-                        scan_row<true, PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, twice, y, akey, best, labb,
-                                                   bestu, queue, tid, gmask, o2, t2, l2, n_hash);
+                        scan_row<true, PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, twice, y, goff, akey, best,
+                                                   labb, bestu, queue, tid, gmask, o2, t2, l2, n_hash);
                         labx = (labx & ~twice) | (winner_labels<BD>(labb, tid, twice) & twice);
                     }
                 } else {
                     best_reset<BD>(best, tid, U);
-                    scan_row<true, PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, akey, best, labb, bestu,
-                                               queue, tid, gmask, once, twice, labx, hub ? n_hash_hub : n_hash);
+                    scan_row<true, PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, goff, akey, best, labb,
+                                               bestu, queue, tid, gmask, once, twice, labx,
+                                               hub ? n_hash_hub : n_hash);
                     labx = winner_labels<BD>(labb, tid, once);
                 }
             }
@@ -349,14 +355,19 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
             if (blockIdx.x == 0) A.sync[(L + 1) % 3] = 0;
         }
         grid_barrier(A.sync, nblocks);
-        const uint32_t grew = *(volatile uint32_t*)(A.sync + (L % 3));
-        const uint32_t err = *(volatile uint32_t*)(A.sync + 6);
-        if (!grew || err) break;
+        // one reader per block, so that every thread of a block leaves the
+        // level loop at the same level
+        if (tid == 0) {
+            const uint32_t grew = *(volatile uint32_t*)(A.sync + (L % 3));
+            const uint32_t err = *(volatile uint32_t*)(A.sync + 6);
+            s_stop = (!grew || err) ? 1u : 0u;
+        }
+        __syncthreads();
+        if (s_stop) break;
         if (++L > A.n + 1) {
             if (tid == 0 && blockIdx.x == 0) atomicOr(A.sync + 6, 2u);
             break;
         }
-        __syncthreads();
     }
     if (tid == 0 && blockIdx.x == 0) A.sync[7] = (uint32_t)L;
     // work counters (one atomic per warp and counter)
@@ -401,14 +412,21 @@ __global__ void k_hub_init(int64_t nh, int Wb, uint64_t* hubnew, uint64_t* hubbe
     }
 }
 
+// root of every tree of this launch in every graph (one graph unless voff)
 __global__ void k_bfs_roots(int64_t n, int Wb, int w0, int64_t K, uint64_t S, int64_t tree0, uint64_t* vis,
-                            uint64_t* fr0, int32_t* parents)
+                            uint64_t* fr0, int32_t* parents, const int32_t* voff, int64_t G)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // tree within this launch
-    int64_t tb = 64 * (int64_t)w0 + i;                          // tree within the batch
-    if (i >= 64 * (int64_t)Wb || tb >= K) return;
-    uint64_t key = sb_tree_key(S, tree0 + tb);
-    uint32_t r = sb_root(key, n);
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per = 64 * (int64_t)Wb;
+    if (x >= per * G) return;
+    const int64_t g = x / per;
+    const int64_t i = x - g * per;      // tree within this launch
+    const int64_t tb = 64 * (int64_t)w0 + i;  // tree within the batch
+    if (tb >= K) return;
+    const uint64_t key = sb_tree_key(S, tree0 + tb);
+    const int64_t base = voff ? voff[g] : 0;
+    const int64_t ng = voff ? voff[g + 1] - voff[g] : n;
+    const uint32_t r = (uint32_t)(base + sb_root(key, ng));
     int w = (int)(i >> 6);
     unsigned long long bit = 1ull << (i & 63);
     atomicOr((unsigned long long*)(vis + (int64_t)r * Wb + w), bit);
@@ -416,48 +434,58 @@ __global__ void k_bfs_roots(int64_t n, int Wb, int w0, int64_t K, uint64_t S, in
     if (parents) parents[tb * n + r] = -1;
 }
 
-__global__ void k_flip(const uint64_t* lab, int W, uint64_t* flipw)
+// canonical flip per graph and word: the raw label of the graph's vertex 0
+__global__ void k_flip(const uint64_t* lab, int W, uint64_t* flipw, const int32_t* voff, int64_t G)
 {
-    int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w < W) flipw[w] = lab[w];  // row of vertex 0
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= (int64_t)W * G) return;
+    const int64_t g = x / W;
+    const int w = (int)(x - g * W);
+    flipw[x] = lab[(voff ? (int64_t)voff[g] : 0) * W + w];
 }
 
-// H_t = sum of weights of vertices whose canonical label is 1 (mod 2^64).
-// Block: 64 lanes per word bit x 4 vertex strides; grid.y = word.
+// H_t = sum of weights of vertices whose canonical label is 1 (mod 2^64),
+// per graph.  Block: 64 lanes per word bit x 4 vertex strides; grid.y = word.
+// Sums are flushed with integer atomics (order-free) when the graph changes.
 #define HASH_VCHUNK 2048
 __global__ void __launch_bounds__(256) k_state_hash(const uint64_t* __restrict__ lab, int64_t n, int W,
                                                     const uint64_t* __restrict__ flipw,
                                                     const uint64_t* __restrict__ weight,
+                                                    const int32_t* __restrict__ vgid, int64_t KP,
                                                     unsigned long long* __restrict__ H)
 {
-    __shared__ uint64_t part[256];
     const int w = blockIdx.y;
     const int b = threadIdx.x & 63, sub = threadIdx.x >> 6;
-    const uint64_t fl = flipw[w];
     const int64_t v0 = (int64_t)blockIdx.x * HASH_VCHUNK;
     const int64_t v1 = min(n, v0 + HASH_VCHUNK);
-    uint64_t acc = 0;
+    int64_t gcur = -1;
+    uint64_t fl = 0, acc = 0;
     for (int64_t v = v0 + sub; v < v1; v += 4) {
+        const int64_t g = vgid ? vgid[v] : 0;
+        if (g != gcur) {
+            if (acc) atomicAdd(H + gcur * KP + 64 * w + b, (unsigned long long)acc);
+            acc = 0;
+            gcur = g;
+            fl = flipw[g * W + w];
+        }
         const uint64_t x = lab[v * W + w] ^ fl;
         const uint64_t wt = weight[v];
         acc += ((x >> b) & 1ull) ? wt : 0ull;
     }
-    part[threadIdx.x] = acc;
-    __syncthreads();
-    if (sub == 0) {
-        acc = part[b] + part[b + 64] + part[b + 128] + part[b + 192];
-        if (acc) atomicAdd(H + 64 * w + b, (unsigned long long)acc);
-    }
+    if (acc) atomicAdd(H + gcur * KP + 64 * w + b, (unsigned long long)acc);
 }
 
 __global__ void k_canon_out(const uint64_t* __restrict__ lab, int64_t total, int W, int64_t K,
-                            const uint64_t* __restrict__ flipw, uint64_t* __restrict__ out)
+                            const uint64_t* __restrict__ flipw, const int32_t* __restrict__ vgid,
+                            uint64_t* __restrict__ out)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        int w = (int)(i % W);
+        const int64_t v = i / W;
+        const int w = (int)(i - v * W);
+        const int64_t g = vgid ? vgid[v] : 0;
         int64_t trees = K - 64 * (int64_t)w;
         uint64_t active = trees >= 64 ? ~0ull : ((1ull << trees) - 1ull);
-        out[i] = (lab[i] ^ flipw[w]) & active;
+        out[i] = (lab[i] ^ flipw[g * W + w]) & active;
     }
 }
 
@@ -553,6 +581,100 @@ __global__ void k_fold_stats(const uint32_t* sync, unsigned long long* acc)
     acc[5] += *(const unsigned long long*)(sync + 14);
 }
 
+// Frustration counts of a batch of graphs: each group of lanes walks one
+// contiguous edge range; carry-save batches never cross a graph boundary, and
+// the counters are flushed (integer atomics) into counts[g * KP + tree] at
+// every boundary and at the end.
+template <int G>
+__global__ void __launch_bounds__(SC_THREADS) k_score_seg(const int2* __restrict__ edges, int64_t m,
+                                                          const uint64_t* __restrict__ lab, int Wt, int w0, int Wb,
+                                                          const int32_t* __restrict__ eoff, int64_t ngraphs,
+                                                          int64_t KP, uint32_t* __restrict__ counts)
+{
+    constexpr int NG = SC_THREADS / G;
+    const int tid = threadIdx.x;
+    const int gl = tid & (G - 1);
+    const bool act = gl < Wb;
+    const int64_t groups = (int64_t)gridDim.x * NG;
+    const int64_t gid = (int64_t)blockIdx.x * NG + tid / G;
+    const int64_t per = sb_cdiv(m, groups);
+    const int64_t e0 = gid * per, e1 = min(m, e0 + per);
+    if (!act || e0 >= e1) return;
+    const uint64_t* __restrict__ lw = lab + w0 + gl;
+    // graph of the first edge
+    int64_t g = 0;
+    {
+        int64_t lo = 0, hi = ngraphs - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if ((int64_t)eoff[mid] <= e0) lo = mid;
+            else hi = mid - 1;
+        }
+        g = lo;
+    }
+    uint64_t ones = 0, twos = 0, fours = 0;
+    uint64_t P[SC_PLANES];
+#pragma unroll
+    for (int b = 0; b < SC_PLANES; b++) P[b] = 0;
+    int64_t e = e0;
+    while (e < e1) {
+        const int64_t gend = min(e1, (int64_t)eoff[g + 1]);
+        while (e < gend) {
+            uint64_t x[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                x[k] = 0;
+                if (e + k < gend) {
+                    const int2 ed = edges[e + k];
+                    const uint32_t vv = (uint32_t)ed.y & SB_ID_MASK;
+                    x[k] = lw[(int64_t)ed.x * Wt] ^ lw[(int64_t)vv * Wt] ^ (ed.y < 0 ? ~0ull : 0ull);
+                }
+            }
+            e = min(gend, e + 8);
+            uint64_t twosA, twosB, foursA, foursB, eights;
+            csa(twosA, ones, ones, x[0], x[1]);
+            csa(twosB, ones, ones, x[2], x[3]);
+            csa(foursA, twos, twos, twosA, twosB);
+            csa(twosA, ones, ones, x[4], x[5]);
+            csa(twosB, ones, ones, x[6], x[7]);
+            csa(foursB, twos, twos, twosA, twosB);
+            csa(eights, fours, fours, foursA, foursB);
+            uint64_t cy = eights;
+#pragma unroll
+            for (int b = 0; b < SC_PLANES; b++) {
+                const uint64_t t = P[b] & cy;
+                P[b] ^= cy;
+                cy = t;
+            }
+        }
+        // flush graph g
+        for (int t = 0; t < 64; t++) {
+            uint32_t hi = 0;
+#pragma unroll
+            for (int b = 0; b < SC_PLANES; b++) hi |= (uint32_t)((P[b] >> t) & 1ull) << b;
+            const uint32_t val = 8u * hi + 4u * (uint32_t)((fours >> t) & 1ull) + 2u * (uint32_t)((twos >> t) & 1ull) +
+                                 (uint32_t)((ones >> t) & 1ull);
+            if (val) atomicAdd(counts + g * KP + 64 * (w0 + gl) + t, val);
+        }
+        ones = twos = fours = 0;
+#pragma unroll
+        for (int b = 0; b < SC_PLANES; b++) P[b] = 0;
+        g++;
+    }
+}
+
+static const void* score_seg_kernel(int G)
+{
+    switch (G) {
+    case 1: return (const void*)k_score_seg<1>;
+    case 2: return (const void*)k_score_seg<2>;
+    case 4: return (const void*)k_score_seg<4>;
+    case 8: return (const void*)k_score_seg<8>;
+    case 16: return (const void*)k_score_seg<16>;
+    default: return (const void*)k_score_seg<32>;
+    }
+}
+
 // --------------------------------------------------------------- host side
 static int group_for(int Wb)
 {
@@ -617,8 +739,10 @@ static sb_status run_bfs(sb_ctx* c, int w0, int Wb, int32_t* parents)
         k_hub_init<<<gh, 256, 0, c->stream>>>(c->n_hubs, Wb, c->hubnew, c->hubbest);
         SB_TRY(sb_after_launch(c, "k_hub_init"));
     }
-    k_bfs_roots<<<(unsigned)sb_cdiv(64 * Wb, 256), 256, 0, c->stream>>>(n, Wb, w0, c->K, sb_seed_key(c->seed),
-                                                                        c->tree_begin, c->vis, c->fr0, parents);
+    const int64_t ngraphs = c->batch_G > 0 ? c->batch_G : 1;
+    k_bfs_roots<<<(unsigned)sb_cdiv(64 * Wb * ngraphs, 256), 256, 0, c->stream>>>(
+        n, Wb, w0, c->K, sb_seed_key(c->seed), c->tree_begin, c->vis, c->fr0, parents,
+        c->batch_G > 0 ? c->b_voff : nullptr, ngraphs);
     SB_TRY(sb_after_launch(c, "k_bfs_roots"));
     SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync, 0, sizeof(uint32_t) * 16, c->stream));
     BfsArgs A;
@@ -642,6 +766,7 @@ static sb_status run_bfs(sb_ctx* c, int w0, int Wb, int32_t* parents)
     A.n = n;
     A.S = sb_seed_key(c->seed);
     A.tree0 = c->tree_begin;
+    A.vgoff = c->batch_G > 0 ? c->vgoff : nullptr;
     void* args[] = {&A};
     {
         SbProf prof(c, SB_PROF_BFS);
@@ -685,9 +810,10 @@ extern "C" sb_status sb_sample_trees(sb_ctx* c, uint64_t seed, int64_t tree_begi
     sb_dfree(c, c->flipw);
     sb_dfree(c, c->hashes);
     sb_dfree(c, c->counts);
-    c->flipw = (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * W);
-    c->hashes = (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * 64 * W);
-    c->counts = (int32_t*)sb_dalloc(c, sizeof(int32_t) * 64 * W);
+    const int64_t G = c->batch_G > 0 ? c->batch_G : 1;  // per-graph results in a batch
+    c->flipw = (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * W * G);
+    c->hashes = (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * 64 * W * G);
+    c->counts = (int32_t*)sb_dalloc(c, sizeof(int32_t) * 64 * W * G);
     size_t words = (size_t)n * Wb_max;
     if (c->bfs_cap_words < words) {
         sb_dfree(c, c->vis);
@@ -720,13 +846,15 @@ extern "C" sb_status sb_sample_trees(sb_ctx* c, uint64_t seed, int64_t tree_begi
         int Wb = W - w0 < SB_WORDS_MAX ? W - w0 : SB_WORDS_MAX;
         SB_TRY(run_bfs(c, w0, Wb, parents_out));
     }
-    k_flip<<<1, 64, 0, c->stream>>>(c->labels, W, c->flipw);
+    k_flip<<<(unsigned)sb_cdiv((int64_t)W * G, 256), 256, 0, c->stream>>>(c->labels, W, c->flipw,
+                                                                          c->batch_G > 0 ? c->b_voff : nullptr, G);
     SB_TRY(sb_after_launch(c, "k_flip"));
-    SB_CHECK_CUDA(c, cudaMemsetAsync(c->hashes, 0, sizeof(uint64_t) * 64 * W, c->stream));
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->hashes, 0, sizeof(uint64_t) * 64 * W * G, c->stream));
     {
         SbProf prof(c, SB_PROF_HASH);
         dim3 hg((unsigned)sb_cdiv(n, HASH_VCHUNK), (unsigned)W);
         k_state_hash<<<hg, 256, 0, c->stream>>>(c->labels, n, W, c->flipw, c->vweight,
+                                                c->batch_G > 0 ? c->vgid : nullptr, 64 * (int64_t)W,
                                                 (unsigned long long*)c->hashes);
         SB_TRY(sb_after_launch(c, "k_state_hash"));
     }
@@ -738,8 +866,32 @@ extern "C" sb_status sb_sample_trees(sb_ctx* c, uint64_t seed, int64_t tree_begi
 sb_status sb_score_batch(sb_ctx* c)
 {
     if (c->counts_valid) return SB_OK;
-    SB_CHECK_CUDA(c, cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 64 * c->W, c->stream));
-    if (c->m > 0) {
+    const int64_t ngraphs = c->batch_G > 0 ? c->batch_G : 1;
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 64 * c->W * ngraphs, c->stream));
+    if (c->m > 0 && c->batch_G > 0) {
+        for (int w0 = 0; w0 < c->W; w0 += SB_WORDS_MAX) {
+            int Wb = c->W - w0 < SB_WORDS_MAX ? c->W - w0 : SB_WORDS_MAX;
+            int G = group_for(Wb);
+            const void* fn = score_seg_kernel(G);
+            int per_sm = 0;
+            SB_CHECK_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SC_THREADS, 0));
+            int64_t blocks = (int64_t)c->num_sms * (per_sm > 0 ? per_sm : 1);
+            int64_t min_blocks = sb_cdiv(c->m, (int64_t)(SC_THREADS / G) * 8 * ((1 << SC_PLANES) - 1));
+            if (blocks < min_blocks) blocks = min_blocks;
+            const int2* e = c->edges;
+            int64_t m = c->m;
+            const uint64_t* lab = c->labels;
+            int Wt = c->W;
+            const int32_t* eoff = c->b_eoff;
+            int64_t ng = c->batch_G;
+            int64_t KP = 64 * (int64_t)c->W;
+            uint32_t* cnt = (uint32_t*)c->counts;
+            void* args[] = {(void*)&e, &m, (void*)&lab, &Wt, &w0, &Wb, (void*)&eoff, &ng, &KP, &cnt};
+            SbProf prof(c, SB_PROF_SCORE);
+            SB_CHECK_CUDA(c, cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(SC_THREADS), args, 0, c->stream));
+            SB_TRY(sb_after_launch(c, "k_score_seg"));
+        }
+    } else if (c->m > 0) {
         for (int w0 = 0; w0 < c->W; w0 += SB_WORDS_MAX) {
             int Wb = c->W - w0 < SB_WORDS_MAX ? c->W - w0 : SB_WORDS_MAX;
             int G = group_for(Wb);
@@ -772,6 +924,18 @@ extern "C" sb_status sb_frustration(sb_ctx* c, int32_t* counts_out, uint64_t* ha
     SB_CHECK_CUDA(c, cudaSetDevice(c->device));
     SB_TRY(check_sync_error(c));
     SB_TRY(sb_score_batch(c));
+    if (c->batch_G > 0) {
+        // per graph: K entries, packed graph after graph
+        const size_t KP = 64 * (size_t)c->W, K = (size_t)c->K, G = (size_t)c->batch_G;
+        if (counts_out)
+            SB_CHECK_CUDA(c, cudaMemcpy2DAsync(counts_out, K * sizeof(int32_t), c->counts, KP * sizeof(int32_t),
+                                               K * sizeof(int32_t), G, cudaMemcpyDefault, c->stream));
+        if (hashes_out)
+            SB_CHECK_CUDA(c, cudaMemcpy2DAsync(hashes_out, K * sizeof(uint64_t), c->hashes, KP * sizeof(uint64_t),
+                                               K * sizeof(uint64_t), G, cudaMemcpyDefault, c->stream));
+        SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+        return SB_OK;
+    }
     if (counts_out) SB_TRY(sb_copy_out(c, counts_out, c->counts, sizeof(int32_t) * c->K));
     if (hashes_out) SB_TRY(sb_copy_out(c, hashes_out, c->hashes, sizeof(uint64_t) * c->K));
     return SB_OK;
@@ -788,7 +952,8 @@ extern "C" sb_status sb_label(sb_ctx* c, uint64_t* labels_out)
     uint64_t* tmp = (uint64_t*)sb_dalloc(c, bytes);
     if (!tmp) return sb_fail(c, SB_ERR_OOM, "label export");
     unsigned g = (unsigned)std::min<int64_t>(sb_cdiv(total, 256), (int64_t)c->num_sms * 16);
-    k_canon_out<<<g, 256, 0, c->stream>>>(c->labels, total, c->W, c->K, c->flipw, tmp);
+    k_canon_out<<<g, 256, 0, c->stream>>>(c->labels, total, c->W, c->K, c->flipw,
+                                          c->batch_G > 0 ? c->vgid : nullptr, tmp);
     sb_status st = sb_after_launch(c, "k_canon_out");
     if (st == SB_OK) st = sb_copy_out(c, labels_out, tmp, bytes);
     cudaStreamSynchronize(c->stream);

@@ -386,3 +386,181 @@ extern "C" sb_status sb_cloud_state(sb_ctx* c, int64_t idx, uint64_t* bits_out)
     sb_dfree(c, tmp);
     return st;
 }
+
+// ------------------------------------------------------ clouds of a batch
+// One block per graph of a batch: the K trees of the graph are sorted by
+// (hash, tree); every tree whose hash equals its run leader's is compared with
+// the leader bit for bit over the graph's vertices, and a tree that differs
+// starts its own state (matched, if possible, against the earlier differing
+// trees of the run).  Output per graph: number of states, min S, and the
+// states in order of first appearance.
+#define BC_MAXK 1024
+#define BC_THREADS 256
+
+__device__ __forceinline__ uint32_t bc_bit(const uint64_t* lab, int W, const uint64_t* flip, int64_t v, int t)
+{
+    const int w = t >> 6;
+    return (uint32_t)(((lab[v * W + w] ^ flip[w]) >> (t & 63)) & 1ull);
+}
+
+// 1 when trees a and b of the graph have equal canonical labels (whole warp)
+__device__ bool bc_same(const uint64_t* lab, int W, const uint64_t* flip, int64_t v0, int64_t v1, int a, int b)
+{
+    uint32_t diff = 0;
+    for (int64_t v = v0 + (threadIdx.x & 31); v < v1; v += 32) diff |= bc_bit(lab, W, flip, v, a) ^ bc_bit(lab, W, flip, v, b);
+    return __all_sync(0xffffffffu, diff == 0);
+}
+
+__global__ void __launch_bounds__(BC_THREADS)
+    k_batch_cloud(const uint64_t* __restrict__ hashes, const int32_t* __restrict__ counts, int64_t KP, int K,
+                  int64_t tree0, const uint64_t* __restrict__ lab, int W, const uint64_t* __restrict__ flipw,
+                  const int32_t* __restrict__ voff, int32_t* __restrict__ nstates_out, int32_t* __restrict__ frmin_out,
+                  sb_cloud_entry* __restrict__ entries)
+{
+    __shared__ uint64_t key[BC_MAXK];
+    __shared__ int32_t idx[BC_MAXK];
+    __shared__ int32_t lead[BC_MAXK];   // sorted position -> position of its run leader
+    __shared__ int32_t state[BC_MAXK];  // tree -> tree that represents its state
+    __shared__ int32_t cnt[BC_MAXK];    // representative tree -> trees in its state
+    __shared__ int32_t rank[BC_MAXK];   // representative tree -> output position
+    __shared__ int32_t s_min, s_ns;
+    const int64_t g = blockIdx.x;
+    const uint64_t* flip = flipw + g * W;
+    const int64_t v0 = voff[g], v1 = voff[g + 1];
+    int P = 1;
+    while (P < K) P <<= 1;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_min = 0x7FFFFFFF;
+        s_ns = 0;
+    }
+    for (int i = tid; i < P; i += BC_THREADS) {
+        key[i] = i < K ? hashes[g * KP + i] : ~0ull;
+        idx[i] = i < K ? i : 0x7FFFFFFF;
+        if (i < K) {
+            cnt[i] = 0;
+            state[i] = i;
+        }
+    }
+    __syncthreads();
+    // bitonic sort by (key, idx)
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < P; i += BC_THREADS) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const bool up = (i & k) == 0;
+                    const bool gt = key[i] > key[p] || (key[i] == key[p] && idx[i] > idx[p]);
+                    if (gt == up) {
+                        const uint64_t tk = key[i];
+                        key[i] = key[p];
+                        key[p] = tk;
+                        const int32_t ti = idx[i];
+                        idx[i] = idx[p];
+                        idx[p] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    // run leaders: inclusive max-scan of head positions
+    for (int i = tid; i < K; i += BC_THREADS) lead[i] = (i == 0 || key[i] != key[i - 1]) ? i : -1;
+    __syncthreads();
+    for (int d = 1; d < K; d <<= 1) {
+        int32_t tmp[BC_MAXK / BC_THREADS];
+        int q = 0;
+        for (int i = tid; i < K; i += BC_THREADS, q++) tmp[q] = (i >= d) ? max(lead[i], lead[i - d]) : lead[i];
+        __syncthreads();
+        q = 0;
+        for (int i = tid; i < K; i += BC_THREADS, q++) lead[i] = tmp[q];
+        __syncthreads();
+    }
+    // compare every non-leader with its leader (one warp per tree)
+    const int warp = tid >> 5, nwarps = BC_THREADS / 32;
+    for (int i = warp; i < K; i += nwarps) {
+        const int li = lead[i];
+        if (li == i) continue;
+        const bool same = bc_same(lab, W, flip, v0, v1, idx[i], idx[li]);
+        if ((tid & 31) == 0) state[idx[i]] = same ? idx[li] : -1;  // -1: differs (hash collision)
+    }
+    __syncthreads();
+    // rare path: trees that differ from their leader, matched in sorted order
+    // against the earlier differing trees of the same run
+    if (warp == 0) {
+        for (int i = 0; i < K; i++) {
+            if (state[idx[i]] != -1) continue;
+            int rep = idx[i];
+            for (int j = lead[i] + 1; j < i; j++) {
+                const int tj = idx[j];
+                if (state[tj] == tj && bc_same(lab, W, flip, v0, v1, idx[i], tj)) {
+                    rep = tj;
+                    break;
+                }
+            }
+            __syncwarp();
+            if ((tid & 31) == 0) state[idx[i]] = rep;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < K; t += BC_THREADS) {
+        atomicAdd(&cnt[state[t]], 1);
+        atomicMin(&s_min, counts[g * KP + t]);
+    }
+    __syncthreads();
+    // output positions: representatives in tree order
+    if (tid == 0) {
+        int r = 0;
+        for (int t = 0; t < K; t++) {
+            rank[t] = (state[t] == t) ? r : -1;
+            if (state[t] == t) r++;
+        }
+        s_ns = r;
+    }
+    __syncthreads();
+    if (entries)
+        for (int t = tid; t < K; t += BC_THREADS)
+            if (state[t] == t) {
+                sb_cloud_entry e;
+                e.hash = hashes[g * KP + t];
+                e.S = counts[g * KP + t];
+                e.count = cnt[t];
+                e.first_tree = tree0 + t;
+                entries[g * (int64_t)K + rank[t]] = e;
+            }
+    if (tid == 0) {
+        nstates_out[g] = s_ns;
+        frmin_out[g] = s_min;
+    }
+}
+
+extern "C" sb_status sb_batch_cloud(sb_ctx* c, int32_t* n_states_out, int32_t* fr_min_out, sb_cloud_entry* entries_out)
+{
+    if (!c || !n_states_out || !fr_min_out) return SB_ERR_ARG;
+    if (!c->has_graph || c->batch_G <= 0) return sb_fail(c, SB_ERR_STATE, "no batch of graphs loaded");
+    if (!c->has_batch) return sb_fail(c, SB_ERR_STATE, "no sampled trees");
+    if (c->K > BC_MAXK) return sb_fail(c, SB_ERR_ARG, "batch clouds need K <= %d", BC_MAXK);
+    SB_CHECK_CUDA(c, cudaSetDevice(c->device));
+    SB_TRY(sb_score_batch(c));
+    const int64_t G = c->batch_G;
+    int32_t* ns = (int32_t*)sb_dalloc(c, sizeof(int32_t) * (size_t)G);
+    int32_t* fm = (int32_t*)sb_dalloc(c, sizeof(int32_t) * (size_t)G);
+    sb_cloud_entry* ent = entries_out ? (sb_cloud_entry*)sb_dalloc(c, sizeof(sb_cloud_entry) * (size_t)G * c->K) : nullptr;
+    sb_status st = SB_OK;
+    if (!ns || !fm || (entries_out && !ent)) st = sb_fail(c, SB_ERR_OOM, "batch cloud output");
+    if (st == SB_OK) {
+        SbProf prof(c, SB_PROF_CLOUD);
+        k_batch_cloud<<<(unsigned)G, BC_THREADS, 0, c->stream>>>(c->hashes, c->counts, 64 * (int64_t)c->W, (int)c->K,
+                                                                c->tree_begin, c->labels, c->W, c->flipw, c->b_voff,
+                                                                ns, fm, ent);
+        st = sb_after_launch(c, "k_batch_cloud");
+    }
+    if (st == SB_OK) st = sb_copy_out(c, n_states_out, ns, sizeof(int32_t) * (size_t)G);
+    if (st == SB_OK) st = sb_copy_out(c, fr_min_out, fm, sizeof(int32_t) * (size_t)G);
+    if (st == SB_OK && ent) st = sb_copy_out(c, entries_out, ent, sizeof(sb_cloud_entry) * (size_t)G * c->K);
+    cudaStreamSynchronize(c->stream);
+    sb_dfree(c, ns);
+    sb_dfree(c, fm);
+    sb_dfree(c, ent);
+    return st;
+}

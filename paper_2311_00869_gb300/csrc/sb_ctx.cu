@@ -238,6 +238,13 @@ void sb_release_graph(sb_ctx* c)
     SB_FREE(gl_hub_vertex);
     SB_FREE(gl_hub_count);
     SB_FREE(vweight);
+    SB_FREE(b_voff);
+    SB_FREE(b_eoff);
+    SB_FREE(vgid);
+    SB_FREE(vgoff);
+    c->batch_G = 0;
+    c->h_voff.clear();
+    c->h_eoff.clear();
     c->has_graph = false;
     c->n = c->m = c->n_items = c->n_hubs = 0;
     c->n_gl_items = c->n_gl_hubs = c->n_gl_partials = 0;

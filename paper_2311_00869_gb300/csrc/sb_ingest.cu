@@ -4,6 +4,8 @@
 // Paper: the appendix "Implementation" paragraph (input cleaning: duplicates,
 // self-loops, inconsistencies, invalid signs), the dataset tables (the LCC of
 // each graph is used), and the complexity section (CSR storage).
+#include <vector>
+
 #include "sb_internal.cuh"
 
 enum { ERRC_RANGE = 1, ERRC_SELF = 2, ERRC_SIGN = 3 };
@@ -270,10 +272,11 @@ __global__ void k_items(const int32_t* __restrict__ rowptr, int64_t n, int chunk
     }
 }
 
-__global__ void k_vweight(uint64_t* w, int64_t n)
+// state-hash weight of each vertex, by its id inside its own graph
+__global__ void k_vweight(uint64_t* w, int64_t n, const int32_t* __restrict__ vgoff)
 {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-        w[v] = sb_weight((uint32_t)v);
+        w[v] = sb_weight((uint32_t)(v - (vgoff ? vgoff[v] : 0)));
 }
 
 __global__ void k_split_edges(const int2* __restrict__ e, int64_t m, int32_t* u, int32_t* v, int8_t* neg)
@@ -292,6 +295,93 @@ __global__ void k_split_col(const int32_t* __restrict__ col, int64_t k, int32_t*
         uint32_t x = (uint32_t)col[i];
         if (c) c[i] = (int32_t)(x & SB_ID_MASK);
         if (neg) neg[i] = (int8_t)(x >> 31);
+    }
+}
+
+// ------------------------------------------------------ batches of graphs
+// index g with off[g] <= x < off[g+1], for nondecreasing off[0..G]
+template <class T>
+__device__ __forceinline__ int64_t seg_of(const T* off, int64_t G, int64_t x)
+{
+    int64_t lo = 0, hi = G - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if ((int64_t)off[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// local ids of edge i (graph g: eofs[g] <= i < eofs[g+1]) -> ids of the union;
+// an id outside [0, nv_g) becomes -1 so that validation reports a range error
+__global__ void k_globalize(int32_t* src, int32_t* dst, int64_t m, const int64_t* __restrict__ eofs,
+                            const int64_t* __restrict__ voff, int64_t G)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = seg_of(eofs, G, i);
+        const int64_t nv = voff[g + 1] - voff[g];
+        const int32_t a = src[i], b = dst[i];
+        src[i] = (a >= 0 && a < nv) ? (int32_t)(voff[g] + a) : -1;
+        dst[i] = (b >= 0 && b < nv) ? (int32_t)(voff[g] + b) : -1;
+    }
+}
+
+// largest component per graph (ties: smallest root) and components per graph
+__global__ void k_uf_best_batch(const int32_t* __restrict__ size, int64_t n, const int64_t* __restrict__ voff,
+                                int64_t G, unsigned long long* best, uint32_t* ncomp)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t sz = size[v];
+        if (sz > 0) {
+            const int64_t g = seg_of(voff, G, v);
+            atomicMax(best + g, ((unsigned long long)sz << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)v));
+            atomicAdd(ncomp + g, 1u);
+        }
+    }
+}
+
+__global__ void k_keep_vertices_batch(const int32_t* __restrict__ root, int64_t n, const int64_t* __restrict__ voff,
+                                      int64_t G, const unsigned long long* __restrict__ best, int32_t* __restrict__ keep)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = seg_of(voff, G, v);
+        const int32_t br = (int32_t)(0xFFFFFFFFu - (uint32_t)(best[g] & 0xFFFFFFFFull));
+        keep[v] = root[v] == br ? 1 : 0;
+    }
+}
+
+// first cleaned vertex of each graph: the exclusive count of kept vertices
+// before the graph's first input vertex
+__global__ void k_batch_vbounds(const int32_t* __restrict__ newid, const int64_t* __restrict__ voff, int64_t G,
+                                int64_t n, int64_t n1, int32_t* __restrict__ voff_out)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g <= G; g += (int64_t)gridDim.x * blockDim.x)
+        voff_out[g] = voff[g] < n ? newid[voff[g]] : (int32_t)n1;
+}
+
+__global__ void k_batch_vgid(const int32_t* __restrict__ voff_out, int64_t G, int64_t n1, int32_t* __restrict__ vgid,
+                             int32_t* __restrict__ vgoff)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n1; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = seg_of(voff_out, G, v);
+        vgid[v] = (int32_t)g;
+        vgoff[v] = voff_out[g];
+    }
+}
+
+// first edge of each graph in the (u, v)-sorted edge list
+__global__ void k_batch_ebounds(const int2* __restrict__ edges, int64_t m, const int32_t* __restrict__ voff_out,
+                                int64_t G, int32_t* __restrict__ eoff)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g <= G; g += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x = voff_out[g];
+        int64_t lo = 0, hi = m;  // first edge with u >= x
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (edges[mid].x < x) lo = mid + 1;
+            else hi = mid;
+        }
+        eoff[g] = (int32_t)lo;
     }
 }
 
@@ -384,9 +474,17 @@ static sb_status build_items(sb_ctx* c, const int32_t* deg, int64_t n, int chunk
     return sb_after_launch(c, "k_items");
 }
 
+// A batch of G graphs loaded as one disjoint union: graph g owns input
+// vertices [voff[g], voff[g+1]) and input edges [eofs[g], eofs[g+1]) (host).
+struct BatchIn {
+    int64_t G;
+    const int64_t* voff;
+    const int64_t* eofs;
+};
+
 static sb_status load_graph_impl(sb_ctx* c, int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
                                  const int8_t* sign, uint32_t flags, int64_t* n_out, int64_t* m_out,
-                                 int32_t* vmap_out)
+                                 int32_t* vmap_out, const BatchIn* B = nullptr)
 {
     IngestTmp T(c);
     int nb = bits_for(n - 1);
@@ -402,6 +500,17 @@ static sb_status load_graph_impl(sb_ctx* c, int64_t n, int64_t m, const int32_t*
         SB_CHECK_CUDA(c, cudaMemcpyAsync(d_src, src, sizeof(int32_t) * m, cudaMemcpyDefault, c->stream));
         SB_CHECK_CUDA(c, cudaMemcpyAsync(d_dst, dst, sizeof(int32_t) * m, cudaMemcpyDefault, c->stream));
         SB_CHECK_CUDA(c, cudaMemcpyAsync(d_sign, sign, sizeof(int8_t) * m, cudaMemcpyDefault, c->stream));
+    }
+    int64_t* d_bvoff = nullptr;
+    int64_t* d_beofs = nullptr;
+    if (B) {
+        d_bvoff = T.get<int64_t>(B->G + 1);
+        d_beofs = T.get<int64_t>(B->G + 1);
+        if (!d_bvoff || !d_beofs) return sb_fail(c, SB_ERR_OOM, "batch offsets");
+        SB_CHECK_CUDA(c, cudaMemcpyAsync(d_bvoff, B->voff, sizeof(int64_t) * (B->G + 1), cudaMemcpyHostToDevice, c->stream));
+        SB_CHECK_CUDA(c, cudaMemcpyAsync(d_beofs, B->eofs, sizeof(int64_t) * (B->G + 1), cudaMemcpyHostToDevice, c->stream));
+        k_globalize<<<grid_for(c, m), 256, 0, c->stream>>>(d_src, d_dst, m, d_beofs, d_bvoff, B->G);
+        SB_TRY(sb_after_launch(c, "k_globalize"));
     }
     unsigned long long init[8] = {~0ull, 0, 0, 0, 0, 0, 0, 0};
     SB_CHECK_CUDA(c, cudaMemcpyAsync(scal, init, sizeof(init), cudaMemcpyHostToDevice, c->stream));
@@ -449,23 +558,45 @@ static sb_status load_graph_impl(sb_ctx* c, int64_t n, int64_t m, const int32_t*
     SB_TRY(sb_after_launch(c, "k_uf_hook"));
     k_uf_sizes<<<gn, 256, 0, c->stream>>>(par, n, size);
     SB_TRY(sb_after_launch(c, "k_uf_sizes"));
-    k_uf_best<<<gn, 256, 0, c->stream>>>(size, n, scal + 1, scal + 2);
-    SB_TRY(sb_after_launch(c, "k_uf_best"));
-    unsigned long long hs[3];
-    SB_CHECK_CUDA(c, cudaMemcpyAsync(hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, c->stream));
-    SB_CHECK_CUDA(c, cudaMemcpyAsync(&hflags, flags_d, sizeof(hflags), cudaMemcpyDeviceToHost, c->stream));
-    SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (hflags & 4u) return sb_fail(c, SB_ERR_DEVICE_CHECK, "union-find retry limit reached");
-    if (hs[2] > 1 && !(flags & SB_LOAD_LCC))
-        return sb_fail(c, SB_ERR_DISCONNECTED, "graph has %llu components", (unsigned long long)hs[2]);
-    // relabel the kept component
     int32_t* keep = T.get<int32_t>(n);
     int32_t* newid = T.get<int32_t>(n);
     int32_t* ekeep = T.get<int32_t>(m1);
     int32_t* epos = T.get<int32_t>(m1);
     if (!keep || !newid || !ekeep || !epos) return sb_fail(c, SB_ERR_OOM, "ingest scratch");
-    k_keep_vertices<<<gn, 256, 0, c->stream>>>(par, n, scal + 1, keep);
-    SB_TRY(sb_after_launch(c, "k_keep_vertices"));
+    if (!B) {
+        k_uf_best<<<gn, 256, 0, c->stream>>>(size, n, scal + 1, scal + 2);
+        SB_TRY(sb_after_launch(c, "k_uf_best"));
+        unsigned long long hs[3];
+        SB_CHECK_CUDA(c, cudaMemcpyAsync(hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, c->stream));
+        SB_CHECK_CUDA(c, cudaMemcpyAsync(&hflags, flags_d, sizeof(hflags), cudaMemcpyDeviceToHost, c->stream));
+        SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (hflags & 4u) return sb_fail(c, SB_ERR_DEVICE_CHECK, "union-find retry limit reached");
+        if (hs[2] > 1 && !(flags & SB_LOAD_LCC))
+            return sb_fail(c, SB_ERR_DISCONNECTED, "graph has %llu components", (unsigned long long)hs[2]);
+        // relabel the kept component
+        k_keep_vertices<<<gn, 256, 0, c->stream>>>(par, n, scal + 1, keep);
+        SB_TRY(sb_after_launch(c, "k_keep_vertices"));
+    } else {
+        unsigned long long* bestg = T.get<unsigned long long>(B->G);
+        uint32_t* ncompg = T.get<uint32_t>(B->G);
+        if (!bestg || !ncompg) return sb_fail(c, SB_ERR_OOM, "batch scratch");
+        SB_CHECK_CUDA(c, cudaMemsetAsync(bestg, 0, sizeof(unsigned long long) * B->G, c->stream));
+        SB_CHECK_CUDA(c, cudaMemsetAsync(ncompg, 0, sizeof(uint32_t) * B->G, c->stream));
+        k_uf_best_batch<<<gn, 256, 0, c->stream>>>(size, n, d_bvoff, B->G, bestg, ncompg);
+        SB_TRY(sb_after_launch(c, "k_uf_best_batch"));
+        std::vector<uint32_t> hcomp(B->G);
+        SB_CHECK_CUDA(c, cudaMemcpyAsync(hcomp.data(), ncompg, sizeof(uint32_t) * B->G, cudaMemcpyDeviceToHost,
+                                         c->stream));
+        SB_CHECK_CUDA(c, cudaMemcpyAsync(&hflags, flags_d, sizeof(hflags), cudaMemcpyDeviceToHost, c->stream));
+        SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (hflags & 4u) return sb_fail(c, SB_ERR_DEVICE_CHECK, "union-find retry limit reached");
+        if (!(flags & SB_LOAD_LCC))
+            for (int64_t g = 0; g < B->G; g++)
+                if (hcomp[g] > 1)
+                    return sb_fail(c, SB_ERR_DISCONNECTED, "graph %lld has %u components", (long long)g, hcomp[g]);
+        k_keep_vertices_batch<<<gn, 256, 0, c->stream>>>(par, n, d_bvoff, B->G, bestg, keep);
+        SB_TRY(sb_after_launch(c, "k_keep_vertices_batch"));
+    }
     SB_TRY(sb_scan_i32(c, keep, newid, n, tot + 1));
     if (vmap_out) {
         int32_t* vm = T.get<int32_t>(n);
@@ -513,7 +644,31 @@ static sb_status load_graph_impl(sb_ctx* c, int64_t n, int64_t m, const int32_t*
     SB_TRY(sb_scan_i32(c, low, lfirst, n1, nullptr));
     k_fill_lower<<<gm2, 256, 0, c->stream>>>(lkeys, m2, nb2, c->rowptr, lfirst, c->col);
     SB_TRY(sb_after_launch(c, "k_fill_lower"));
-    k_vweight<<<gn1, 256, 0, c->stream>>>(c->vweight, n1);
+    if (B) {
+        const int64_t G = B->G;
+        c->b_voff = (int32_t*)sb_dalloc(c, sizeof(int32_t) * (size_t)(G + 1));
+        c->b_eoff = (int32_t*)sb_dalloc(c, sizeof(int32_t) * (size_t)(G + 1));
+        c->vgid = (int32_t*)sb_dalloc(c, sizeof(int32_t) * (size_t)n1);
+        c->vgoff = (int32_t*)sb_dalloc(c, sizeof(int32_t) * (size_t)n1);
+        if (!c->b_voff || !c->b_eoff || !c->vgid || !c->vgoff) return sb_fail(c, SB_ERR_OOM, "batch storage");
+        unsigned gg = grid_for(c, G + 1);
+        k_batch_vbounds<<<gg, 256, 0, c->stream>>>(newid, d_bvoff, G, n, n1, c->b_voff);
+        SB_TRY(sb_after_launch(c, "k_batch_vbounds"));
+        k_batch_vgid<<<gn1, 256, 0, c->stream>>>(c->b_voff, G, n1, c->vgid, c->vgoff);
+        SB_TRY(sb_after_launch(c, "k_batch_vgid"));
+        k_batch_ebounds<<<gg, 256, 0, c->stream>>>(c->edges, m2, c->b_voff, G, c->b_eoff);
+        SB_TRY(sb_after_launch(c, "k_batch_ebounds"));
+        std::vector<int32_t> hv(G + 1), he(G + 1);
+        SB_CHECK_CUDA(c, cudaMemcpyAsync(hv.data(), c->b_voff, sizeof(int32_t) * (G + 1), cudaMemcpyDeviceToHost,
+                                         c->stream));
+        SB_CHECK_CUDA(c, cudaMemcpyAsync(he.data(), c->b_eoff, sizeof(int32_t) * (G + 1), cudaMemcpyDeviceToHost,
+                                         c->stream));
+        SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->h_voff.assign(hv.begin(), hv.end());
+        c->h_eoff.assign(he.begin(), he.end());
+        c->batch_G = G;
+    }
+    k_vweight<<<gn1, 256, 0, c->stream>>>(c->vweight, n1, c->vgoff);
     SB_TRY(sb_after_launch(c, "k_vweight"));
     c->n = n1;
     c->m = m2;
@@ -581,5 +736,39 @@ extern "C" sb_status sb_graph_csr(sb_ctx* c, int32_t* rowptr_out, int32_t* col_o
     SB_TRY(sb_after_launch(c, "k_split_col"));
     SB_TRY(sb_copy_out(c, col_out, cc, sizeof(int32_t) * k));
     SB_TRY(sb_copy_out(c, neg_out, g, sizeof(int8_t) * k));
+    return SB_OK;
+}
+
+extern "C" sb_status sb_load_batch(sb_ctx* c, int64_t n_graphs, const int64_t* nv, const int64_t* eofs,
+                                   const int32_t* src, const int32_t* dst, const int8_t* sign, uint32_t flags,
+                                   int64_t* nv_out, int64_t* m_out)
+{
+    if (!c) return SB_ERR_ARG;
+    if (n_graphs < 1 || n_graphs > (1ll << 24) || !nv || !eofs || eofs[0] != 0 ||
+        (flags & ~(SB_LOAD_LCC | SB_LOAD_MERGE_DUP)))
+        return sb_fail(c, SB_ERR_ARG, "sb_load_batch: bad argument");
+    std::vector<int64_t> voff(n_graphs + 1, 0);
+    for (int64_t g = 0; g < n_graphs; g++) {
+        if (nv[g] < 1 || eofs[g + 1] < eofs[g]) return sb_fail(c, SB_ERR_ARG, "sb_load_batch: graph %lld", (long long)g);
+        voff[g + 1] = voff[g] + nv[g];
+    }
+    const int64_t n = voff[n_graphs], m = eofs[n_graphs];
+    if (n > 0x7FFFFFFF || 2 * m >= 0x7FFFFFFF || (m > 0 && (!src || !dst || !sign)))
+        return sb_fail(c, SB_ERR_ARG, "sb_load_batch: batch too large (n=%lld m=%lld)", (long long)n, (long long)m);
+    SB_CHECK_CUDA(c, cudaSetDevice(c->device));
+    SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+    sb_release_graph(c);
+    SbProf prof(c, SB_PROF_INGEST);
+    BatchIn B{n_graphs, voff.data(), eofs};
+    int64_t n1 = 0, m1 = 0;
+    sb_status st = load_graph_impl(c, n, m, src, dst, sign, flags, &n1, &m1, nullptr, &B);
+    if (st != SB_OK) {
+        sb_release_graph(c);
+        return st;
+    }
+    for (int64_t g = 0; g < n_graphs; g++) {
+        if (nv_out) nv_out[g] = c->h_voff[g + 1] - c->h_voff[g];
+        if (m_out) m_out[g] = c->h_eoff[g + 1] - c->h_eoff[g];
+    }
     return SB_OK;
 }

@@ -106,6 +106,14 @@ struct sb_ctx {
     int64_t n_gl_hubs = 0, n_gl_partials = 0;
     uint64_t* vweight = nullptr;  // n: state-hash weights
 
+    // batch of graphs (disjoint union; 0 = a single graph)
+    int64_t batch_G = 0;
+    int32_t* b_voff = nullptr;    // G + 1: first vertex of each graph (cleaned ids)
+    int32_t* b_eoff = nullptr;    // G + 1: first edge of each graph in `edges`
+    int32_t* vgid = nullptr;      // n: graph of each vertex (batch only)
+    int32_t* vgoff = nullptr;     // n: first vertex of the vertex's graph (batch only)
+    std::vector<int64_t> h_voff, h_eoff;
+
     // last sampled batch
     bool has_batch = false;
     uint64_t seed = 0;

@@ -1,0 +1,61 @@
+"""GPU parity of the batch of uneven graphs (one disjoint union): every graph's
+cleaning, trees, labels, counts, hashes and cloud equal what the oracle
+gives for that graph alone."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _graphs(count, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        n = int(np.exp(rng.uniform(np.log(6), np.log(400))))
+        out.append(synth.chung_lu(n, 6.0, 2.5, float(rng.uniform(0.05, 0.3)), seed=int(rng.integers(1 << 30))))
+    # a balanced graph and an isolated-vertex graph (LCC of a single vertex)
+    n, u, v, s, _ = synth.planted_balanced(30, 40, seed=5)
+    out.append((n, u, v, s))
+    out.append((3, np.array([], np.int32), np.array([], np.int32), np.array([], np.int8)))
+    return out
+
+
+@pytest.mark.parametrize("K", [64, 130])
+def test_batch_matches_per_graph_oracle(K):
+    import paper_2311_00869_gb300 as P
+
+    graphs = _graphs(23, seed=K)
+    sb = P.SignedBal(0)
+    nv, mv = sb.load_batch(graphs)
+    refs = [O.clean_graph(*g) for g in graphs]
+    assert list(nv) == [r.n for r in refs] and list(mv) == [r.m for r in refs]
+    # the union's edge list is the graphs' edge lists, shifted
+    eu, ev, eneg = (t.cpu().numpy() for t in sb.graph_edges())
+    off = np.concatenate([[0], np.cumsum(nv)])
+    eoff = np.concatenate([[0], np.cumsum(mv)])
+    for g, r in enumerate(refs):
+        sl = slice(eoff[g], eoff[g + 1])
+        assert np.array_equal(eu[sl] - off[g], r.eu) and np.array_equal(ev[sl] - off[g], r.ev)
+        assert np.array_equal(eneg[sl], r.eneg)
+    sb.sample_trees(7, 3, K)
+    counts, hashes = sb.batch_frustration()
+    counts, hashes = counts.cpu().numpy(), hashes.cpu().numpy().view(np.uint64)
+    labels = P.unpack_labels(sb.label(), K)  # (K, n_total)
+    cl = sb.batch_cloud()
+    for g, r in enumerate(refs):
+        ref = O.sample(r, 7, 3, K)
+        assert np.array_equal(counts[g], ref["counts"]), g
+        assert np.array_equal(hashes[g], ref["hashes"]), g
+        assert np.array_equal(labels[:, off[g]:off[g + 1]], ref["labels"]), g
+        rc = O.cloud(ref["labels"], ref["counts"], t0=3)
+        assert cl["n_states"][g] == rc["S"].shape[0]
+        assert cl["fr_min"][g] == ref["counts"].min()
+        e = cl["entries"][g]
+        assert np.array_equal(e["first_tree"], rc["first_tree"])
+        assert np.array_equal(e["count"], rc["count"])
+        assert np.array_equal(e["S"], rc["S"])
+        assert np.array_equal(e["hash"], rc["H"])
+    sb.close()
