@@ -263,6 +263,30 @@ sb_status sb_graphL_descent(sb_ctx* ctx, const float* gamma0, float* gamma_out, 
  */
 sb_status sb_graphL_round(sb_ctx* ctx, const float* gamma, int32_t R, int32_t* F_out, uint64_t* flip_out);
 
+/*
+ * Allocation-free variant of sb_graphL_fwd (the paper has no counterpart;
+ * this is an integration convenience).  For callers that cannot allocate
+ * device memory at call time: code that runs while a CUDA graph is being
+ * captured, hosts that hand the library a fixed memory budget up front, or
+ * plugins whose host application owns every allocator.  It takes no context
+ * and calls no cudaMalloc, cudaFree or allocating library routine; its
+ * scratch is a fixed device array of about 2.4 MiB that every GPU loading the
+ * library keeps until exit.
+ *   edges: device array of m (u, v | neg << 31) int32 pairs, the cleaned edge
+ *          list in the layout of the context's own (u < v; neg = 1 for a
+ *          negative edge; sb_graph_edges gives its parts).
+ *   gamma (n x R float32), loss_out (R), F_out (R, nullable): device, as for
+ *          sb_graphL_fwd, on the current CUDA device.
+ *   cuda_stream: cudaStream_t (NULL = legacy default stream).
+ * Limits: 1 <= R <= 1024 and 0 <= m < 2^31, else SB_ERR_ARG and nothing runs.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) and should come before any stream capture.  All
+ * calls on a device share the scratch and it keeps the last call's contents:
+ * calls that overlap on the GPU race and must be serialised by the caller.
+ */
+sb_status sb_graphL_fwd_static(const int32_t* edges, int64_t m, const float* gamma, int32_t R, float* loss_out,
+                               int32_t* F_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -42,6 +42,7 @@ SIGNATURES = {
     "sb_graphL_bwd": (i32, [P, P, i32, P, P]),
     "sb_graphL_descent": (i32, [P, P, P, i32, f32, i32, i32, P, P, P]),
     "sb_graphL_round": (i32, [P, P, i32, P, P]),
+    "sb_graphL_fwd_static": (i32, [P, i64, P, i32, P, P, P]),
 }
 
 _lib = None

@@ -458,3 +458,58 @@ extern "C" sb_status sb_graphL_descent(sb_ctx* c, const float* gamma0, float* ga
     if (F_final) SB_TRY(sb_graphL_round(c, gamma_out, R, F_final, nullptr));
     return SB_OK;
 }
+
+// ------------------------------------------- allocation-free relaxed loss
+// sb_graphL_fwd_static runs the same two kernels as sb_graphL_fwd, but its
+// scratch (per-block partial sums and the discrete-loss accumulators) lives in
+// the fixed array below instead of context memory, so the call allocates
+// nothing.  Every GPU that loads this library holds the array until the
+// process exits.  All calls on a device share it and it keeps the last call's
+// contents: the accumulators are cleared at the start of each call, and calls
+// that overlap on the GPU (other streams, other host threads) race on it.
+#define GL_STATIC_BLOCKS 304
+#define GL_STATIC_RMAX 1024
+static __device__ __align__(256) unsigned char g_gl_static_scratch[sizeof(double) * GL_STATIC_BLOCKS * GL_STATIC_RMAX +
+                                                                   sizeof(int32_t) * GL_STATIC_RMAX];
+
+#include <mutex>
+static std::mutex g_static_mu;
+static void* g_static_ptr[256];  // device address of the array, per device
+
+extern "C" sb_status sb_graphL_fwd_static(const int32_t* edges, int64_t m, const float* gamma, int32_t R,
+                                          float* loss_out, int32_t* F_out, void* cuda_stream)
+{
+    if (R < 1 || R > GL_STATIC_RMAX || m < 0 || m >= (1ll << 31) || !gamma || !loss_out || (m > 0 && !edges))
+        return SB_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+        cudaGetLastError();
+        return SB_ERR_CUDA;
+    }
+    void* base = nullptr;
+    {
+        // first call on this device: look up the array's device address with
+        // the device current (the host-side symbol is not a device address)
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        if (!g_static_ptr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_gl_static_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return SB_ERR_CUDA;
+            }
+            g_static_ptr[dev] = p;
+        }
+        base = g_static_ptr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    double* red = (double*)base;
+    int32_t* Facc = (int32_t*)(red + (size_t)GL_STATIC_BLOCKS * GL_STATIC_RMAX);
+    if (cudaMemsetAsync(Facc, 0, sizeof(int32_t) * (size_t)R, st) != cudaSuccess) {
+        cudaGetLastError();
+        return SB_ERR_CUDA;
+    }
+    k_gl_fwd<<<GL_STATIC_BLOCKS, GL_THREADS, 0, st>>>((const int2*)edges, m, gamma, R, red, Facc);
+    k_gl_fwd_final<<<(unsigned)sb_cdiv(R, 256), 256, 0, st>>>(red, GL_STATIC_BLOCKS, R, m, loss_out, Facc, F_out);
+    if (cudaGetLastError() != cudaSuccess) return SB_ERR_CUDA;
+    return SB_OK;
+}
