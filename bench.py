@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--scale", type=int, default=20)
     ap.add_argument("--edges-log2", type=int, default=24)
     ap.add_argument("--no-extras", action="store_true", help="skip the plain / graphL / e2e / cpu legs")
+    ap.add_argument("--leg", default="bpp", choices=["bpp", "graphl", "batch"],
+                    help="bpp: the graphBpp line (default); graphl: graphL descent only; batch: uneven batch")
+    ap.add_argument("--R", type=int, default=256, help="graphL start points (--leg graphl)")
+    ap.add_argument("--graphs", type=int, default=4096, help="graphs in the uneven batch (--leg batch)")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default tuning knobs")
     return ap.parse_args()
 
 
@@ -191,6 +196,12 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.leg == "batch":
+        import synth
+
+        t = time.perf_counter()  # the process pool starts before any CUDA call
+        args.batch_graphs = list(synth.uneven_batch(count=args.graphs, workers=os.cpu_count() or 1))
+        args.batch_gen_s = time.perf_counter() - t
     import torch
 
     rank, world, local = dist_env()
@@ -202,10 +213,34 @@ def main():
         dist.init_process_group("nccl")
     import paper_2311_00869_gb300 as P
 
+    if args.leg == "batch":
+        return batch_leg(args, P)
     n, u, v, s = workload(args)
     stream = torch.cuda.current_stream()
     sb = P.SignedBal(local, stream=stream)
     n1, m1, _ = sb.load_graph(n, u, v, s)
+    if args.leg == "graphl":
+        tuned = {"default": True}
+        if not args.no_tune:
+            from paper_2311_00869_gb300 import autotune
+
+            tuned = autotune.tune(sb, K=TREES, R=args.R)
+        res = graphl_leg(P, sb, n1, m1, R=args.R, steps=args.steps)
+        res["tuning"] = tuned
+        line = {"leg": "graphl", "metric": "graphL steps/s", "value": res["graphl_steps_per_s"], "unit": "steps/s",
+                "n_gpus": 1, "steps": args.steps, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                "config": config_dict(args, n1, m1, 1), "extras": res}
+        print(json.dumps(line), flush=True)
+        sb.close()
+        return 0
+    tuned = {"default": True}
+    if not args.no_tune:
+        try:
+            from paper_2311_00869_gb300 import autotune
+
+            tuned = autotune.tune(sb, K=TREES)
+        except Exception as e:  # tuning only changes speed
+            tuned = {"error": repr(e)}
     steps_total = args.warmup + args.steps
     sb.cloud_reset(max_states=(steps_total + 2) * TREES + 64)
     counts = torch.empty(TREES, dtype=torch.int32, device="cuda")
@@ -249,7 +284,8 @@ def main():
     launches = sum(c for _, c in prof.values())
 
     cl, fr_min = sb.cloud()
-    extras = {"fr_min": int(fr_min), "distinct_states": int(cl["S"].shape[0])}
+    extras = {"fr_min": int(fr_min), "distinct_states": int(cl["S"].shape[0]), "tuning": tuned,
+              "bfs_stats": sb.stats()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -264,6 +300,9 @@ def main():
         except Exception as e:  # a failing side leg must not hide the main number
             extras["plain_error"] = repr(e)
         try:
+            from paper_2311_00869_gb300 import autotune
+
+            extras["graphl_tuning"] = autotune.tune(sb, K=TREES, R=256)
             extras.update(graphl_leg(P, sb, n1, m1))
         except Exception as e:
             extras["graphl_error"] = repr(e)
@@ -354,7 +393,7 @@ def graphl_leg(P, sb, n, m, R=256, steps=50, alpha=0.05):
 
     g0 = torch.from_numpy(synth.gamma0(n, R, seed=0)).cuda()
     out = torch.empty_like(g0)
-    sb.graphL_descent(g0, alpha, 5, out=out)  # warm-up
+    sb.graphL_descent(g0, alpha, steps, out=out)  # warm-up: captures the step loop as a CUDA graph
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sb.profile_read()
@@ -397,6 +436,64 @@ def e2e_leg(P, sb, n, u, v, s, steps=3):
     d2h = hc.numel() * 4 + hh.numel() * 8 + int(cl["S"].shape[0]) * 24
     return {"value": steps * TREES * m1 / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "includes": "H2D of the COO, ingest, sample, count, cloud, D2H"}
+
+
+
+def batch_leg(args, P):
+    """Uneven batch: `--graphs` Chung-Lu graphs (vertex counts log-uniform in
+    [50, 50000], mean degree 8, exponent 2.5, 5-30% negative), 256 trees per
+    graph in one sampling call over the disjoint union, per-graph clouds, and
+    32 graphL start points per graph for `--steps` descent steps."""
+    import torch
+
+    import synth
+
+    graphs, gen_s = args.batch_graphs, args.batch_gen_s
+    sb = P.SignedBal(0)
+    nv, mv = sb.load_batch(graphs)
+    K, R = 256, 32
+    n_tot, m_tot = int(nv.sum()), int(mv.sum())
+    for i in range(args.warmup):
+        sb.sample_trees(SEED, i * K, K)
+        sb.batch_cloud(want_entries=False)
+    torch.cuda.synchronize()
+    sb.profile_read()
+    sb.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for i in range(args.steps):
+        sb.sample_trees(SEED, (args.warmup + i) * K, K)
+        cl = sb.batch_cloud(want_entries=False)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    prof = sb.profile_read()
+    g0 = torch.from_numpy(synth.gamma0(n_tot, R, seed=0)).cuda()
+    out = torch.empty_like(g0)
+    steps_gl = 100
+    sb.graphL_descent(g0, 0.05, steps_gl, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    _, _, _, F_final = sb.graphL_descent(g0, 0.05, steps_gl, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    gl_ms = e0.elapsed_time(e1)
+    line = {
+        "leg": "batch", "metric": "graphBpp edge-evals/s over the uneven batch", "value": K * m_tot / (ms / 1000.0),
+        "unit": "edge-evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"uneven_batch_{args.graphs}_chung_lu", "graphs": args.graphs, "n_total": n_tot,
+                   "m_total": m_tot, "trees_per_graph": K, "graphl_R": R, "generation_s": gen_s},
+        "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
+        "graphl_steps_per_s": steps_gl / (gl_ms / 1000.0),
+        "fr_min_median": float(np.median(cl["fr_min"])),
+        "states_median": float(np.median(cl["n_states"])),
+        "graphl_F_median": float(np.median(F_final.cpu().numpy())),
+    }
+    print(json.dumps(line), flush=True)
+    sb.close()
+    return 0
 
 
 if __name__ == "__main__":

@@ -100,6 +100,19 @@ sb_status sb_profile(sb_ctx* ctx, int enable);
    timing is off. */
 sb_status sb_profile_read(sb_ctx* ctx, double* ms_out, int64_t* launches_out);
 
+/* Run-time tuning knobs (chosen by the package's autotuner; 0 = default):
+   SB_TUNE_BFS_WORDS         64-tree words grown per BFS launch (1..32; 32)
+   SB_TUNE_SCORE_BLOCKS_SM   scorer blocks per SM (0 = as many as fit)
+   SB_TUNE_GL_LANES          graphL lanes per row segment: 8 (32 columns)
+                             or 32 (128 columns) when R % 4 == 0 (8)
+   Results never depend on them.  sb_get_tuning returns the current value. */
+#define SB_TUNE_BFS_WORDS 0
+#define SB_TUNE_SCORE_BLOCKS_SM 1
+#define SB_TUNE_GL_LANES 2
+#define SB_TUNE_N 3
+sb_status sb_set_tuning(sb_ctx* ctx, int32_t knob, int64_t value);
+sb_status sb_get_tuning(sb_ctx* ctx, int32_t knob, int64_t* value);
+
 /* Work counters of the last sb_sample_trees call (host array, n entries,
    n <= SB_STATS_N): [0] BFS levels (largest over its launches), [1] BFS
    launches, [2] neighbour entries scanned (per vertex-word lane),
@@ -152,9 +165,12 @@ sb_status sb_graph_csr(sb_ctx* ctx, int32_t* rowptr_out, int32_t* col_out, int8_
  * tree t of graph g is exactly tree t of sb_load_graph(graph g) with the
  * same seed (ids are taken inside each graph).  sb_frustration then returns
  * G x K counts / hashes (graph-major), and sb_label canonicalises each graph
- * by its own vertex 0.  sb_graphL_* treat the union as one graph (the graphs
- * share no edge, so the loss and gradient are per-graph sums).  sb_cloud is
- * not available on a batch: use sb_batch_cloud.
+ * by its own vertex 0.  graphL runs on the union (the graphs share no edge,
+ * so rows and gradients are per graph); every per-column output becomes
+ * per (graph, column), G x R graph-major: sb_graphL_fwd's loss and F,
+ * sb_graphL_round's F, and sb_graphL_descent's exps, F_trace rows and
+ * F_final, whose renormalisation is decided per graph and column.
+ * sb_cloud is not available on a batch: use sb_batch_cloud.
  */
 sb_status sb_load_batch(sb_ctx* ctx, int64_t n_graphs, const int64_t* nv, const int64_t* eofs, const int32_t* src,
                         const int32_t* dst, const int8_t* sign, uint32_t flags, int64_t* nv_out, int64_t* m_out);

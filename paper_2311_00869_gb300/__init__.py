@@ -108,6 +108,7 @@ class SignedBal:
         vmap = np.zeros(n, np.int32) if want_vmap else None
         self._check(self.lib.sb_load_graph(self.h, int(n), m, _ptr(conv[0]), _ptr(conv[1]), _ptr(conv[2]), flags,
                                            ctypes.byref(n_out), ctypes.byref(m_out), _ptr(vmap)))
+        self.batch_G = 0
         self.n, self.m = n_out.value, m_out.value
         return self.n, self.m, vmap
 
@@ -218,11 +219,14 @@ class SignedBal:
         return out
 
     # ---------------------------------------------------------------- graphL
+    def _per_graph(self):
+        return getattr(self, "batch_G", 0) or 1
+
     def graphL_fwd(self, gamma):
         gamma = gamma.contiguous()
         R = gamma.shape[1]
-        loss = torch.empty(R, dtype=torch.float32, device=self.device)
-        F = torch.empty(R, dtype=torch.int32, device=self.device)
+        loss = torch.empty(self._per_graph() * R, dtype=torch.float32, device=self.device)
+        F = torch.empty(self._per_graph() * R, dtype=torch.int32, device=self.device)
         self._check(self.lib.sb_graphL_fwd(self.h, _ptr(gamma), R, _ptr(loss), _ptr(F)))
         return loss, F
 
@@ -237,9 +241,10 @@ class SignedBal:
         gamma0 = gamma0.contiguous()
         R = gamma0.shape[1]
         out = torch.empty_like(gamma0) if out is None else out
-        exps = torch.empty(R, dtype=torch.int32, device=self.device)
-        F_trace = torch.empty((steps, R), dtype=torch.int32, device=self.device) if trace else None
-        F_final = torch.empty(R, dtype=torch.int32, device=self.device)
+        GR = self._per_graph() * R
+        exps = torch.empty(GR, dtype=torch.int32, device=self.device)
+        F_trace = torch.empty((steps, GR), dtype=torch.int32, device=self.device) if trace else None
+        F_final = torch.empty(GR, dtype=torch.int32, device=self.device)
         self._check(self.lib.sb_graphL_descent(self.h, _ptr(gamma0), _ptr(out), R, float(alpha), steps, renorm_log2,
                                                _ptr(exps), _ptr(F_trace), _ptr(F_final)))
         return out, exps, F_trace, F_final
@@ -247,13 +252,27 @@ class SignedBal:
     def graphL_round(self, gamma, want_flip=False):
         gamma = gamma.contiguous()
         R = gamma.shape[1]
-        F = torch.empty(R, dtype=torch.int32, device=self.device)
+        F = torch.empty(self._per_graph() * R, dtype=torch.int32, device=self.device)
         flip = torch.empty((R, (self.m + 63) // 64), dtype=torch.int64, device=self.device) if want_flip else None
         self._check(self.lib.sb_graphL_round(self.h, _ptr(gamma), R, _ptr(F), _ptr(flip)))
         return F, flip
 
     def sync(self):
         self._check(self.lib.sb_sync(self.h))
+
+    TUNE_KNOBS = {"bfs_words": 0, "score_blocks_sm": 1, "gl_lanes": 2}
+
+    def set_tuning(self, **knobs):
+        for k, v in knobs.items():
+            self._check(self.lib.sb_set_tuning(self.h, self.TUNE_KNOBS[k], int(v)))
+
+    def get_tuning(self):
+        out = {}
+        for k, i in self.TUNE_KNOBS.items():
+            v = ctypes.c_int64()
+            self._check(self.lib.sb_get_tuning(self.h, i, ctypes.byref(v)))
+            out[k] = v.value
+        return out
 
     def stats(self):
         """Work counters of the last sample_trees call."""

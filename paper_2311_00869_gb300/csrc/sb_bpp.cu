@@ -20,6 +20,7 @@
 
 #define BFS_THREADS 128
 #define BFS_THREADS_PAR 128
+#define BFS_QUEUE_PER_LANE 32  // candidate-queue entries per lane (overflow falls back to per-lane hashing)
 #define SYNC_WORDS 32
 #define BAR_LIMIT_CYCLES (4ll * 1000 * 1000 * 1000)  // ~2 s at 2 GHz
 
@@ -148,14 +149,31 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
                 int pos = group_excl_scan<G>(cnt, gmask, gl, T);
                 if (T == 0) continue;  // same for the whole group
                 nhash += (uint32_t)cnt;
+                const uint32_t u = (c[k] & SB_ID_MASK) - goff;  // id inside the graph
+                const uint32_t hx = u ^ y;
+                if (T > BFS_QUEUE_PER_LANE * G) {
+                    // rare: more candidates than the queue holds; each lane
+                    // hashes its own bits (it alone owns their slots)
+                    for (uint64_t b = f[k]; b;) {
+                        const int t = __ffsll((long long)b) - 1;
+                        b &= b - 1;
+                        const uint32_t h = sb_fmix32(hx + akey[gl * 64 + t]);
+                        const int slot = t * BD + tid;
+                        if (h <= best[slot]) {
+                            best[slot] = h;
+                            labb[slot] = (uint8_t)((l[k] >> t) & 1ull);
+                            if (PAR) bestu[slot] = (int32_t)u;
+                        }
+                    }
+                    __syncwarp(gmask);
+                    continue;
+                }
                 for (uint64_t b = f[k]; b;) {
                     const int t = __ffsll((long long)b) - 1;
                     b &= b - 1;
                     queue[pos++] = (uint16_t)((gl << 7) | (t << 1) | (int)((l[k] >> t) & 1ull));
                 }
                 __syncwarp(gmask);
-                const uint32_t u = (c[k] & SB_ID_MASK) - goff;  // id inside the graph
-                const uint32_t hx = u ^ y;
                 for (int i = gl; i < T; i += G) {
                     const uint32_t e = queue[i];
                     const int ow = (int)(e >> 7), t = (int)((e >> 1) & 63u);
@@ -204,10 +222,10 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
     constexpr int BD = PAR ? BFS_THREADS_PAR : BFS_THREADS;
     extern __shared__ uint32_t smem[];
     uint32_t* akey = smem;                        // Wb * 64 tree salts
-    uint32_t* best = smem + SB_WORDS_MAX * 64;    // 64 x BD running minima
+    uint32_t* best = smem + A.Wb * 64;            // 64 x BD running minima
     uint8_t* labb = (uint8_t*)(best + 64 * BD);   // 64 x BD winners' label bits
-    uint16_t* queues = (uint16_t*)(labb + 64 * BD);  // 64 x G entries per group
-    int32_t* bestu = (int32_t*)(queues + 64 * BD);   // 64 x BD winners (PAR only)
+    uint16_t* queues = (uint16_t*)(labb + 64 * BD);  // BFS_QUEUE_PER_LANE x G entries per group
+    int32_t* bestu = (int32_t*)(queues + BFS_QUEUE_PER_LANE * BD);  // 64 x BD winners (PAR only)
     __shared__ uint32_t s_any, s_stop;
 
     const int tid = threadIdx.x;
@@ -224,7 +242,7 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
 
     const int Wb = A.Wb, Wt = A.Wt, w0 = A.w0;
     const int wofs = w0 + gl;
-    uint16_t* queue = queues + (tid / G) * (64 * G);
+    uint16_t* queue = queues + (tid / G) * (BFS_QUEUE_PER_LANE * G);
     uint32_t n_scan = 0, n_hash = 0, n_pass2 = 0, n_hash_hub = 0;  // work counters
     int L = 1;
     while (true) {
@@ -723,7 +741,7 @@ static sb_status run_bfs(sb_ctx* c, int w0, int Wb, int32_t* parents)
     const int G = group_for(Wb);
     const int BD = par ? BFS_THREADS_PAR : BFS_THREADS;
     const void* fn = par ? bfs_kernel<true>(G) : bfs_kernel<false>(G);
-    size_t smem = sizeof(uint32_t) * (SB_WORDS_MAX * 64 + 64 * BD) + 64 * BD + sizeof(uint16_t) * 64 * BD +
+    size_t smem = sizeof(uint32_t) * ((size_t)Wb * 64 + 64 * BD) + 64 * BD + sizeof(uint16_t) * BFS_QUEUE_PER_LANE * BD +
                   (par ? sizeof(int32_t) * 64 * BD : 0);
     SB_CHECK_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -799,7 +817,8 @@ extern "C" sb_status sb_sample_trees(sb_ctx* c, uint64_t seed, int64_t tree_begi
     SB_TRY(ensure_sync(c));
     const int64_t n = c->n;
     const int W = (int)sb_cdiv(K, 64);
-    const int Wb_max = W < SB_WORDS_MAX ? W : SB_WORDS_MAX;
+    const int WL = c->tune[SB_TUNE_BFS_WORDS] > 0 ? (int)c->tune[SB_TUNE_BFS_WORDS] : SB_WORDS_MAX;  // words per launch
+    const int Wb_max = W < WL ? W : WL;
     // batch storage
     size_t lab_bytes = sizeof(uint64_t) * (size_t)n * W;
     if (c->labels_cap < lab_bytes) {
@@ -842,8 +861,8 @@ extern "C" sb_status sb_sample_trees(sb_ctx* c, uint64_t seed, int64_t tree_begi
     c->counts_valid = false;
     c->batch_in_cloud = false;
     SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync + 16, 0, sizeof(uint32_t) * 16, c->stream));
-    for (int w0 = 0; w0 < W; w0 += SB_WORDS_MAX) {
-        int Wb = W - w0 < SB_WORDS_MAX ? W - w0 : SB_WORDS_MAX;
+    for (int w0 = 0; w0 < W; w0 += WL) {
+        int Wb = W - w0 < WL ? W - w0 : WL;
         SB_TRY(run_bfs(c, w0, Wb, parents_out));
     }
     k_flip<<<(unsigned)sb_cdiv((int64_t)W * G, 256), 256, 0, c->stream>>>(c->labels, W, c->flipw,
@@ -875,6 +894,7 @@ sb_status sb_score_batch(sb_ctx* c)
             const void* fn = score_seg_kernel(G);
             int per_sm = 0;
             SB_CHECK_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SC_THREADS, 0));
+            if (c->tune[SB_TUNE_SCORE_BLOCKS_SM] > 0) per_sm = std::min<int>(per_sm, (int)c->tune[SB_TUNE_SCORE_BLOCKS_SM]);
             int64_t blocks = (int64_t)c->num_sms * (per_sm > 0 ? per_sm : 1);
             int64_t min_blocks = sb_cdiv(c->m, (int64_t)(SC_THREADS / G) * 8 * ((1 << SC_PLANES) - 1));
             if (blocks < min_blocks) blocks = min_blocks;

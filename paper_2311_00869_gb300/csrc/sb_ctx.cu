@@ -55,7 +55,7 @@ static cudaEvent_t ev_get(sb_ctx* c)
 void sb_prof_begin(sb_ctx* c, cudaEvent_t* a)
 {
     *a = nullptr;
-    if (!c->prof_on || c->prof_recs.size() > 200000) return;
+    if (!c->prof_on || c->capturing || c->prof_recs.size() > 200000) return;
     *a = ev_get(c);
     if (*a) cudaEventRecord(*a, c->stream);
 }
@@ -221,7 +221,11 @@ void sb_release_graphl(sb_ctx* c)
     SB_FREE(gl_scale);
     SB_FREE(gl_colmax);
     SB_FREE(gl_misc);
+    if (c->gl_exec) cudaGraphExecDestroy(c->gl_exec);
+    c->gl_exec = nullptr;
+    memset(c->gl_exec_key, 0, sizeof(c->gl_exec_key));
     c->gl_partial_cap = c->gl_red_cap = c->gl_buf_cap = c->gl_misc_cap = 0;
+    c->gl_scale_cap = c->gl_colmax_cap = 0;
 }
 
 void sb_release_graph(sb_ctx* c)
@@ -238,6 +242,9 @@ void sb_release_graph(sb_ctx* c)
     SB_FREE(gl_hub_vertex);
     SB_FREE(gl_hub_count);
     SB_FREE(vweight);
+    if (c->gl_exec) cudaGraphExecDestroy(c->gl_exec);
+    c->gl_exec = nullptr;
+    memset(c->gl_exec_key, 0, sizeof(c->gl_exec_key));
     SB_FREE(b_voff);
     SB_FREE(b_eoff);
     SB_FREE(vgid);
@@ -288,6 +295,9 @@ extern "C" void sb_destroy(sb_ctx* c)
         cudaEventDestroy(r.b);
     }
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->cap_in) cudaEventDestroy(c->cap_in);
+    if (c->cap_out) cudaEventDestroy(c->cap_out);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
 }
 
@@ -299,6 +309,24 @@ extern "C" sb_status sb_set_allocator(sb_ctx* c, sb_alloc_fn alloc, sb_free_fn f
     c->alloc = alloc;
     c->free_fn = free_fn;
     c->alloc_user = user;
+    return SB_OK;
+}
+
+extern "C" sb_status sb_set_tuning(sb_ctx* c, int32_t knob, int64_t value)
+{
+    if (!c || knob < 0 || knob >= SB_TUNE_N || value < 0) return SB_ERR_ARG;
+    if (knob == SB_TUNE_BFS_WORDS && value > SB_WORDS_MAX) return sb_fail(c, SB_ERR_ARG, "at most 32 words per launch");
+    if (knob == SB_TUNE_SCORE_BLOCKS_SM && value > 32) return sb_fail(c, SB_ERR_ARG, "at most 32 blocks per SM");
+    if (knob == SB_TUNE_GL_LANES && value != 0 && value != 8 && value != 32)
+        return sb_fail(c, SB_ERR_ARG, "graphL lanes must be 8 or 32");
+    c->tune[knob] = value;
+    return SB_OK;
+}
+
+extern "C" sb_status sb_get_tuning(sb_ctx* c, int32_t knob, int64_t* value)
+{
+    if (!c || !value || knob < 0 || knob >= SB_TUNE_N) return SB_ERR_ARG;
+    *value = c->tune[knob];
     return SB_OK;
 }
 

@@ -226,11 +226,15 @@ __global__ void k_chunks(const int32_t* __restrict__ deg, int64_t n, int chunk, 
 
 // work items: one per row chunk; split rows get an index and the position of
 // their first chunk among the chunks of split rows
-// sort key placing high-degree rows first (ties by vertex id)
-__global__ void k_degkeys(const int32_t* __restrict__ deg, int64_t n, uint64_t* __restrict__ keys)
+// sort key placing high-degree rows first (ties by vertex id), or, with
+// split_first, the split rows first and every group in vertex order
+__global__ void k_degkeys(const int32_t* __restrict__ deg, int64_t n, uint64_t* __restrict__ keys, int chunk,
+                          int split_first)
 {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-        keys[v] = ((uint64_t)(0x7FFFFFFFu - (uint32_t)deg[v]) << 32) | (uint64_t)v;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t hi = split_first ? (deg[v] > chunk ? 0u : 1u) : (0x7FFFFFFFu - (uint32_t)deg[v]);
+        keys[v] = ((uint64_t)hi << 32) | (uint64_t)v;
+    }
 }
 
 __global__ void k_perm(const uint64_t* __restrict__ keys, int64_t n, const int32_t* __restrict__ nch,
@@ -420,7 +424,9 @@ struct IngestTmp {
 
 // Builds the work items of one chunk size: returns items, split-row vertex
 // list (and optionally first partial slot / chunk count per split row).
-static sb_status build_items(sb_ctx* c, const int32_t* deg, int64_t n, int chunk, bool by_degree,
+// Work items of one chunk size.  order 0: vertex order; 1: descending degree;
+// 2: chunks of split rows first, then whole rows (each in vertex order).
+static sb_status build_items(sb_ctx* c, const int32_t* deg, int64_t n, int chunk, int order,
                              sb_bfs_item** items_out, int64_t* n_items, int32_t** hub_vertex, int64_t* n_hubs,
                              int32_t** hub_first, int32_t** hub_count, int64_t* n_partials)
 {
@@ -437,12 +443,12 @@ static sb_status build_items(sb_ctx* c, const int32_t* deg, int64_t n, int chunk
     k_chunks<<<g, 256, 0, c->stream>>>(deg, n, chunk, nch, split);
     SB_TRY(sb_after_launch(c, "k_chunks"));
     int32_t* perm = nullptr;
-    if (by_degree) {
+    if (order != 0) {
         uint64_t* keys = T.get<uint64_t>(n);
         perm = T.get<int32_t>(n);
         int32_t* nch_sorted = T.get<int32_t>(n);
         if (!keys || !perm || !nch_sorted) return sb_fail(c, SB_ERR_OOM, "item scratch");
-        k_degkeys<<<g, 256, 0, c->stream>>>(deg, n, keys);
+        k_degkeys<<<g, 256, 0, c->stream>>>(deg, n, keys, chunk, order == 2 ? 1 : 0);
         SB_TRY(sb_after_launch(c, "k_degkeys"));
         SB_TRY(sb_radix_sort_u64(c, keys, n, 64));
         k_perm<<<g, 256, 0, c->stream>>>(keys, n, nch, perm, nch_sorted);
@@ -672,9 +678,9 @@ static sb_status load_graph_impl(sb_ctx* c, int64_t n, int64_t m, const int32_t*
     SB_TRY(sb_after_launch(c, "k_vweight"));
     c->n = n1;
     c->m = m2;
-    SB_TRY(build_items(c, deg, n1, SB_BFS_CHUNK, true, &c->items, &c->n_items, &c->hub_vertex, &c->n_hubs, nullptr,
+    SB_TRY(build_items(c, deg, n1, SB_BFS_CHUNK, 1, &c->items, &c->n_items, &c->hub_vertex, &c->n_hubs, nullptr,
                        nullptr, nullptr));
-    SB_TRY(build_items(c, deg, n1, SB_GL_CHUNK, false, &c->gl_items, &c->n_gl_items, &c->gl_hub_vertex,
+    SB_TRY(build_items(c, deg, n1, SB_GL_CHUNK, 2, &c->gl_items, &c->n_gl_items, &c->gl_hub_vertex,
                        &c->n_gl_hubs, &c->gl_hub_first, &c->gl_hub_count, &c->n_gl_partials));
     SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
     c->has_graph = true;

@@ -158,14 +158,26 @@ struct sb_ctx {
     size_t gl_red_cap = 0;
     float* gl_buf = nullptr;       // ping-pong buffer for descent
     size_t gl_buf_cap = 0;
-    float* gl_scale = nullptr;     // per-column pending power-of-two scale
+    float* gl_scale = nullptr;     // per-(graph, column) pending power-of-two scale
+    size_t gl_scale_cap = 0;
     uint32_t* gl_colmax = nullptr;
+    size_t gl_colmax_cap = 0;
     int32_t* gl_misc = nullptr;
     size_t gl_misc_cap = 0;
+
+    // captured descent loop (replayed while its arguments stay the same)
+    cudaGraphExec_t gl_exec = nullptr;
+    uint64_t gl_exec_key[16] = {0};
+    bool capturing = false;
+    cudaStream_t cap_stream = nullptr;  // private stream: capture is not allowed on the legacy stream
+    cudaEvent_t cap_in = nullptr, cap_out = nullptr;
 
     // misc scratch
     void* tmp = nullptr;
     size_t tmp_cap = 0;
+
+    // tuning knobs (SB_TUNE_*)
+    int64_t tune[SB_TUNE_N] = {0, 0, 0};
 
     // profiling: per-family launch counts, optional CUDA-event timing
     int prof_on = 0;

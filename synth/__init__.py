@@ -121,15 +121,28 @@ def chung_lu(n, mean_deg=8.0, gamma=2.5, neg_frac=0.2, seed=1005, i0=1.0):
     return n, perm[u], perm[v], sign
 
 
-def uneven_batch(count=4096, n_lo=50, n_hi=50000, seed=1005):
+def _chung_lu_args(a):
+    return chung_lu(*a)
+
+
+def uneven_batch(count=4096, n_lo=50, n_hi=50000, seed=1005, workers=0):
     """`count` Chung-Lu graphs, vertex counts log-uniform in [n_lo, n_hi],
-    mean degree 8, exponent 2.5, negative fraction U(0.05, 0.30) per graph."""
+    mean degree 8, exponent 2.5, negative fraction U(0.05, 0.30) per graph.
+    workers > 0 draws them in a spawned process pool (same graphs)."""
     rng = _rng(seed)
     ns = np.floor(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), count))).astype(np.int64)
     negs = rng.uniform(0.05, 0.30, count)
     seeds = rng.integers(0, 2**62, count)
-    for i in range(count):
-        yield chung_lu(int(ns[i]), 8.0, 2.5, float(negs[i]), int(seeds[i]))
+    args = [(int(ns[i]), 8.0, 2.5, float(negs[i]), int(seeds[i])) for i in range(count)]
+    if workers > 0:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            yield from ex.map(_chung_lu_args, args, chunksize=16)
+        return
+    for a in args:
+        yield chung_lu(*a)
 
 
 def random_connected(n, extra, neg_frac=0.3, seed=0):

@@ -59,3 +59,41 @@ def test_batch_matches_per_graph_oracle(K):
         assert np.array_equal(e["S"], rc["S"])
         assert np.array_equal(e["hash"], rc["H"])
     sb.close()
+
+
+def test_batch_graphl_per_graph():
+    """graphL on a batch: loss, discrete loss, gradient and descent of every
+    graph equal the per-graph float64 oracle (renormalised per graph)."""
+    import torch
+
+    import paper_2311_00869_gb300 as P
+
+    graphs = _graphs(9, seed=3)
+    sb = P.SignedBal(0)
+    nv, mv = sb.load_batch(graphs)
+    refs = [O.clean_graph(*g) for g in graphs]
+    off = np.concatenate([[0], np.cumsum(nv)])
+    R = 8
+    gam = synth.gamma0(int(off[-1]), R, seed=11)
+    G0 = torch.from_numpy(gam).cuda()
+    loss, F = sb.graphL_fwd(G0)  # G x R in a batch
+    loss = loss.reshape(len(graphs), R).cpu().numpy()
+    F = F.reshape(len(graphs), R).cpu().numpy()
+    out, exps, F_trace, F_final = sb.graphL_descent(G0, 0.05, 60, renorm_log2=16, trace=True)
+    exps = exps.reshape(len(graphs), R).cpu().numpy()
+    F_final = F_final.reshape(len(graphs), R).cpu().numpy()
+    out = out.cpu().numpy()
+    for g, r in enumerate(refs):
+        sl = slice(off[g], off[g + 1])
+        L64, F64 = O.graphl_loss_f64(r, gam[sl].astype(np.float64))
+        prod = np.abs(gam[sl][r.eu].astype(np.float64) * gam[sl][r.ev])
+        assert np.array_equal(F[g], F64), g
+        assert np.all(np.abs(loss[g] - L64) <= 1e-5 * (0.5 * (1.0 + prod)).sum(axis=0) + 1e-6), g
+        ref, rexps, _ = O.graphl_descent_f64(r, gam[sl], 0.05, 60, renorm_log2=16)
+        got = out[sl].astype(np.float64) * np.exp2(exps[g].astype(np.float64))[None, :]
+        want = ref * np.exp2(rexps.astype(np.float64))[None, :]
+        scale = np.abs(want).max(axis=0) + 1e-300
+        assert np.all(np.abs(got - want) <= 1e-3 * scale[None, :]), g
+        oF, _ = O.graphl_round_f32(r, out[sl])
+        assert np.array_equal(F_final[g], oF), g
+    sb.close()
