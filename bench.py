@@ -286,6 +286,12 @@ def main():
     cl, fr_min = sb.cloud()
     extras = {"fr_min": int(fr_min), "distinct_states": int(cl["S"].shape[0]), "tuning": tuned,
               "bfs_stats": sb.stats()}
+    if dist:  # host-side merge of the rank clouds, after the timed region
+        from paper_2311_00869_gb300 import shard
+
+        merged = shard.gather_cloud(cl)
+        extras["distinct_states_all_ranks"] = int(merged["S"].shape[0])
+        extras["fr_min_all_ranks"] = int(merged["S"].min()) if merged["S"].size else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

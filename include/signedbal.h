@@ -61,8 +61,8 @@ typedef void (*sb_free_fn)(void* ptr, void* stream, void* user);
    it, and its 64-bit state hash. */
 typedef struct sb_cloud_entry {
     uint64_t hash;       /* sum of vertex weights over vertices labelled 1, mod 2^64 */
-    int32_t S;           /* edge signs switched to reach the state (Alg. 1 line 7)   */
-    int32_t count;       /* trees that produced the state (Alg. 1 line 13)           */
+    int32_t S;           /* edge signs switched to reach the state (Algorithm 1)   */
+    int32_t count;       /* trees that produced the state (Algorithm 1)           */
     int64_t first_tree;  /* global index of the first such tree                      */
 } sb_cloud_entry;
 
@@ -178,7 +178,7 @@ sb_status sb_load_batch(sb_ctx* ctx, int64_t n_graphs, const int64_t* nv, const 
 /*
  * Frustration cloud of every graph of a batch for the trees of the last
  * sb_sample_trees (K <= 1024): the distinct states of each graph's K trees,
- * checked bit for bit on every hash match (Alg. 1 lines 8-14).  Host or
+ * checked bit for bit on every hash match (Algorithm 1).  Host or
  * device outputs: n_states_out[G], fr_min_out[G] (= min S, Eq. 1), and
  * entries_out[G x K] (nullable): graph g's states at [g*K, g*K + n_states[g])
  * in order of first appearance.
@@ -189,7 +189,7 @@ sb_status sb_batch_cloud(sb_ctx* ctx, int32_t* n_states_out, int32_t* fr_min_out
 
 /*
  * Samples trees [tree_begin, tree_begin + K) and their balanced states
- * (Alg. 1 lines 2 and 6; appendix graphB+ algorithm).  Tree t is the
+ * (Algorithm 1; appendix graphB+ algorithm).  Tree t is the
  * randomized BFS tree defined by
  *     S   = mix64(seed + G),  K_t = mix64(S + (t + 1) G),  G = 0x9E3779B97F4A7C15
  *     root r_t = ((K_t >> 32) * n) >> 32
@@ -211,7 +211,7 @@ sb_status sb_sample_trees(sb_ctx* ctx, uint64_t seed, int64_t tree_begin, int64_
    W = ceil(K / 64); bits of trees >= K are 0.  Host or device. */
 sb_status sb_label(sb_ctx* ctx, uint64_t* labels_out);
 
-/* Alg. 1 line 7 for each tree of the last batch: counts_out[i] = number of
+/* Algorithm 1 for each tree of the last batch: counts_out[i] = number of
    edges whose sign differs between the graph and the state of tree
    tree_begin + i (label(u) XOR label(v) XOR neg).  hashes_out[i] = state
    hash.  Host or device; hashes_out nullable. */
@@ -243,7 +243,7 @@ sb_status sb_cloud_state(sb_ctx* ctx, int64_t idx, uint64_t* bits_out);
 /* ------------------------------------------------------------------ graphL */
 
 /*
- * Relaxed loss of Eq. 3 and discrete loss of Eq. 2 (Alg. 2 lines 5-6) for R
+ * Relaxed loss of Eq. 3 and discrete loss of Eq. 2 (Algorithm 2) for R
  * starting points at once: gamma is n x R float32 row-major (gamma[v*R + r]).
  * loss_out[r] = sum over edges (1 - e_uv G_u G_v) / 2, each undirected edge
  * once; F_out[r] = edges with e_uv theta_u theta_v = -1, theta = +1 iff

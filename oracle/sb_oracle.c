@@ -282,7 +282,7 @@ int or_build_csr(int64_t n, int64_t m, const int32_t* eu, const int32_t* ev, con
 /* ---------------------------------------------------------------- graphBpp */
 
 /*
- * One randomized BFS spanning tree and its balanced state (Alg. 1 line 6 via
+ * One randomized BFS spanning tree and its balanced state (Algorithm 1 via
  * the appendix graphB+ algorithm, restated through Harary's bipartition).
  *
  * Tree t (global index t, seed `seed`):
@@ -363,7 +363,7 @@ int64_t or_tree(int64_t n, const int64_t* rowptr, const int32_t* col, const int8
     return root;
 }
 
-/* Alg. 1 line 7: number of edges whose sign differs between the graph and
+/* Algorithm 1: number of edges whose sign differs between the graph and
    the balanced state, i.e. edges with lab(u) XOR lab(v) XOR neg = 1. */
 int64_t or_frustration(int64_t m, const int32_t* eu, const int32_t* ev, const int8_t* eneg, const uint8_t* clab)
 {
@@ -406,7 +406,7 @@ int or_sample(int64_t n, const int64_t* rowptr, const int32_t* col, const int8_t
 }
 
 /*
- * Frustration cloud (Alg. 1 lines 8-14 and Eq. 1): distinct states among K
+ * Frustration cloud (Algorithm 1 and Eq. 1): distinct states among K
  * trees, keyed by the full canonical labelling.  Entries come out in order of
  * first appearance; for each: first tree index (t0 + i), count C, switch
  * count S, state hash H.  Returns the number of distinct states.  Scratch is
@@ -461,7 +461,7 @@ int64_t or_cloud(int64_t n, int64_t K, int64_t t0, const uint8_t* clab, const in
 
 /*
  * Relaxed loss, Eq. 3: L_r = sum over undirected edges (1 - e_ij G_i G_j) / 2,
- * each edge once; and the discrete loss of Eq. 2 / Alg. 2 line 5 with
+ * each edge once; and the discrete loss of Eq. 2 / Algorithm 2 with
  * theta = +1 when Gamma >= 0, else -1 (the rule of Alg. 2's final loop).
  * gamma is n x R row-major (vertex v, init r at gamma[v*R + r]).
  */
@@ -519,7 +519,7 @@ void or_graphl_grad_f32(int64_t n, const int64_t* rowptr, const int32_t* col, co
  * exps[r] grows by renorm_log2 (renorm_log2 = 0 disables this).  Scaling by a
  * power of two is exact, and the update is linear, so the signs are those of
  * the unscaled run.  F_trace (nullable, steps x R) receives the discrete loss
- * of Alg. 2 line 5 evaluated before each update.
+ * of Algorithm 2 evaluated before each update.
  */
 int or_graphl_descent_f64(int64_t n, const int64_t* rowptr, const int32_t* col, const int8_t* colneg, int64_t m,
                           const int32_t* eu, const int32_t* ev, const int8_t* eneg, double* gamma, int64_t R,

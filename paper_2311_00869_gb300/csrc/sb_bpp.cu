@@ -1,7 +1,7 @@
 // sb_bpp.cu -- graphBpp hot path: batched randomized-BFS tree sampling with
-// parity labelling (Alg. 1 line 6 through the appendix graphB+ algorithm,
+// parity labelling (Algorithm 1 through the appendix graphB+ algorithm,
 // restated with Harary's bipartition, Sec. 2), the state hash that keys the
-// frustration cloud, and the bit-sliced frustration scorer (Alg. 1 line 7).
+// frustration cloud, and the bit-sliced frustration scorer (Algorithm 1).
 //
 // Data layout (vertex-major, 64 trees per uint64 word):
 //   labels[v * W + w]  bit b = parity label of tree 64 w + b at vertex v

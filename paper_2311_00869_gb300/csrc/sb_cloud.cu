@@ -1,4 +1,4 @@
-// sb_cloud.cu -- the frustration cloud (Alg. 1 lines 8-14, Eq. 1): distinct
+// sb_cloud.cu -- the frustration cloud (Algorithm 1, Eq. 1): distinct
 // balanced states with their count C and switch count S.
 //
 // The paper keys its std::map by the state's edge-sign string.  Here a state

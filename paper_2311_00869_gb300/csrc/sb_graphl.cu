@@ -1,6 +1,6 @@
 // sb_graphl.cu -- graphL (Sec. 4, Alg. 2): relaxed loss (Eq. 3), discrete
 // loss (Eq. 2), the adjoint dL/dG_v = -1/2 sum_j e_vj G_j (Eq. 4), the descent
-// update G <- G - alpha dL/dG, and the final rounding (Alg. 2 lines 11-24).
+// update G <- G - alpha dL/dG, and the final rounding (Algorithm 2).
 //
 // Layout: G is n x R float32, row-major (the R starting points of one vertex
 // are contiguous), so a neighbour gather reads a contiguous row segment.
