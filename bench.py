@@ -26,7 +26,6 @@ import os
 import statistics
 import subprocess
 import sys
-import tempfile
 import time
 from concurrent.futures import ThreadPoolExecutor
 
@@ -48,15 +47,21 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--scale", type=int, default=20)
-    ap.add_argument("--edges-log2", type=int, default=24)
+    ap.add_argument("--scale", type=int, default=None, help="R-MAT scale (default 20; 24 for --leg scale24)")
+    ap.add_argument("--edges-log2", type=int, default=None, help="log2 of the edge count (default 24; 27)")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain / graphL / e2e / cpu legs")
-    ap.add_argument("--leg", default="bpp", choices=["bpp", "graphl", "batch"],
-                    help="bpp: the graphBpp line (default); graphl: graphL descent only; batch: uneven batch")
+    ap.add_argument("--leg", default="bpp", choices=["bpp", "graphl", "batch", "scale24"],
+                    help="bpp: the graphBpp line (default); graphl: graphL descent only; batch: uneven batch; "
+                         "scale24: R-MAT 2^24 vertices / 2^27 edges, 4096 trees per step")
     ap.add_argument("--R", type=int, default=256, help="graphL start points (--leg graphl)")
+    ap.add_argument("--gl-steps", type=int, default=500, help="graphL descent steps (--leg graphl)")
     ap.add_argument("--graphs", type=int, default=4096, help="graphs in the uneven batch (--leg batch)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default tuning knobs")
-    return ap.parse_args()
+    args = ap.parse_args()
+    big = args.leg == "scale24"
+    args.scale = args.scale if args.scale is not None else (24 if big else 20)
+    args.edges_log2 = args.edges_log2 if args.edges_log2 is not None else (27 if big else 24)
+    return args
 
 
 def dist_env():
@@ -98,15 +103,18 @@ class ClockSampler:
         self.path = None
 
     def start(self):
+        import threading
+
+        self.lines = []
         try:
-            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
-            os.close(fd)
-            self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
-                                         stderr=subprocess.DEVNULL)
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return
+        self.reader = threading.Thread(target=lambda: self.lines.extend(self.proc.stdout), daemon=True)
+        self.reader.start()
 
     def stop(self):
         if self.proc is None:
@@ -116,10 +124,10 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        self.fh.close()
+        self.reader.join(timeout=5)
         sms, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in list(self.lines):
             p = [x.strip() for x in line.split(",")]
             if len(p) < 9:
                 continue
@@ -131,7 +139,6 @@ class ClockSampler:
             for name, val in zip(names, p[5:9]):
                 if val.lower() == "active":
                     reasons.add(name)
-        os.unlink(self.path)
         if not sms:
             return None
         return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sms)}
@@ -202,6 +209,13 @@ def main():
         t = time.perf_counter()  # the process pool starts before any CUDA call
         args.batch_graphs = list(synth.uneven_batch(count=args.graphs, workers=os.cpu_count() or 1))
         args.batch_gen_s = time.perf_counter() - t
+    if args.leg == "scale24":
+        import synth
+
+        t = time.perf_counter()
+        args.scale_graph = synth.rmat_three_faction(scale=args.scale, m_target=1 << args.edges_log2,
+                                                    workers=os.cpu_count() or 1)
+        args.scale_gen_s = time.perf_counter() - t
     import torch
 
     rank, world, local = dist_env()
@@ -215,6 +229,8 @@ def main():
 
     if args.leg == "batch":
         return batch_leg(args, P)
+    if args.leg == "scale24":
+        return scale_leg(args, P)
     n, u, v, s = workload(args)
     stream = torch.cuda.current_stream()
     sb = P.SignedBal(local, stream=stream)
@@ -225,10 +241,10 @@ def main():
             from paper_2311_00869_gb300 import autotune
 
             tuned = autotune.tune(sb, K=TREES, R=args.R)
-        res = graphl_leg(P, sb, n1, m1, R=args.R, steps=args.steps)
+        res = graphl_leg(P, sb, n1, m1, R=args.R, steps=args.gl_steps)
         res["tuning"] = tuned
         line = {"leg": "graphl", "metric": "graphL steps/s", "value": res["graphl_steps_per_s"], "unit": "steps/s",
-                "n_gpus": 1, "steps": args.steps, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                "n_gpus": 1, "steps": args.gl_steps, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
                 "config": config_dict(args, n1, m1, 1), "extras": res}
         print(json.dumps(line), flush=True)
         sb.close()
@@ -299,7 +315,8 @@ def main():
         "gpu_launches": launches, "clocks": clk,
         "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
     }
-    line["roofline"] = roofline(prof, args.steps, n1, m1)
+    line["roofline"] = roofline(prof, n1, m1, TREES, extras["bfs_stats"], (clk or {}).get("sm_mhz"))
+    extras["roofline_score"] = roofline_family("score", prof, n1, m1, TREES)
     if not args.no_extras and rank == 0:
         try:
             extras.update(plain_leg(sb, m1))
@@ -330,37 +347,99 @@ def main():
     return 0
 
 
-def roofline(prof, steps, n, m):
-    """Dominant kernel family with its algorithmic bytes per launch."""
-    peaks = {}
+def _src_digest(paths):
+    """sha256 of kernel sources with comments and whitespace removed."""
+    import hashlib
+    import re
+
+    h = hashlib.sha256()
+    for rel in paths:
+        txt = open(os.path.join(ROOT, rel)).read()
+        txt = re.sub(r"/\*.*?\*/", " ", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", " ", txt)
+        h.update(" ".join(txt.split()).encode())
+    return h.hexdigest()
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a
+# kernel, from an ncu capture of this bench's own workload (the command is in
+# the matching summary under profiles/).  A figure is reported only while the
+# kernel sources still match the digest taken when it was captured.
+_BPP_SRC = ("paper_2311_00869_gb300/csrc/sb_bpp.cu", "paper_2311_00869_gb300/csrc/sb_internal.cuh")
+NCU_TRAFFIC = {
+    "bfs": (4152176128 + 1842199296, _BPP_SRC, "82438abff86619438a196924fb91e863cc2954543b1f6569062be19bc3723b10"),
+}
+
+
+def _traffic_bytes():
+    out = {}
+    for fam, (nbytes, srcs, digest) in NCU_TRAFFIC.items():
+        try:
+            out[fam] = nbytes if _src_digest(srcs) == digest else None
+        except OSError:
+            out[fam] = None
+    return out
+
+
+NCU_TRAFFIC_BYTES = _traffic_bytes()
+ALU_LANES_PER_SM = 128  # INT32-capable lanes per SM (4 partitions x 32)
+NUM_SMS = 152
+OPS_PER_HASH = 11  # (u ^ y) + key: 2, the 32-bit finaliser: 8, compare: 1
+
+
+def _peaks():
     try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
-        pass
+        return {}
+
+
+def roofline_family(fam, prof, n, m, K, stats=None, sm_mhz=None):
+    """Roofline of one kernel family: HBM-bound families against the measured
+    copy bandwidth with their algorithmic bytes per launch; the BFS against
+    the integer-ALU peak (SMs x INT32 lanes x SM clock) with the hash work the
+    argmin parent rule needs (counted by the kernel) per launch."""
+    peaks = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     src = "measured" if "hbm_gbs" in peaks else "fallback"
-    fam = max(prof, key=lambda k: prof[k][0])
-    ms, launches = prof[fam]
-    W = TREES // 64
-    # algorithmic bytes per launch (see the design notes for the derivation)
+    ms, launches = prof.get(fam, (0.0, 0))
+    if launches == 0 or ms <= 0:
+        return None
+    avg_s = ms / launches / 1000.0
+    if fam == "bfs":
+        if not stats or not stats.get("bfs_launches"):
+            return None
+        hashes = (stats["hashed_candidates"] + stats["hashed_candidates_split_rows"]) / stats["bfs_launches"]
+        mhz = 2070.0
+        peak = NUM_SMS * ALU_LANES_PER_SM * mhz * 1e6 / 1e9  # Gop/s at the maximum SM clock
+        achieved = OPS_PER_HASH * hashes / avg_s / 1e9
+        return {"bound": "alu", "kernel": "k_bfs", "achieved": achieved, "peak": peak,
+                "peak_source": f"derived: {NUM_SMS} SMs x {ALU_LANES_PER_SM} INT32 lanes x {mhz:.0f} MHz",
+                "unit": "Gop/s", "frac": achieved / peak, "traffic": NCU_TRAFFIC_BYTES.get("bfs"),
+                "algorithmic_ops_per_launch": OPS_PER_HASH * hashes, "avg_launch_ms": 1000 * avg_s,
+                "launches": launches, "sm_mhz_median": sm_mhz}
+    W = (K + 63) // 64
     per_launch = {
-        # one CSR scan (2m x 4 B), rowptr-free work items (16 B per row),
-        # labels written once (n x W x 8 B) and the frontier of every vertex
-        # read once per word (n x W x 8 B)
-        "bfs": 2 * m * 4 + 16 * n + 2 * n * W * 8,
         # edge stream (8 B per edge) + every label word read once (n x W x 8 B) + counts
-        "score": 8 * m + n * W * 8 + 4 * TREES,
-        "hash": n * W * 8 + n * 8 + 8 * TREES,
+        "score": 8 * m + n * W * 8 + 4 * K,
+        "hash": n * W * 8 + n * 8 + 8 * K,
         "cloud": n * W * 8 + n * W * 8,
     }.get(fam)
-    if per_launch is None or launches == 0 or ms <= 0:
-        return {"bound": "hbm", "kernel": fam, "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
-                "traffic": None}
-    avg_s = ms / launches / 1000.0
+    if per_launch is None:
+        return None
     achieved = per_launch / avg_s / 1e9
-    return {"bound": "hbm", "kernel": fam, "achieved": achieved, "peak": hbm, "peak_source": src, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None, "algorithmic_bytes_per_launch": per_launch,
+    return {"bound": "hbm", "kernel": {"score": "k_score", "hash": "k_state_hash", "cloud": "cloud"}[fam],
+            "achieved": achieved, "peak": hbm, "peak_source": src, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": NCU_TRAFFIC_BYTES.get(fam), "algorithmic_bytes_per_launch": per_launch,
             "avg_launch_ms": 1000 * avg_s, "launches": launches}
+
+
+def roofline(prof, n, m, K, stats=None, sm_mhz=None):
+    """Roofline object of the dominant kernel family."""
+    fam = max(prof, key=lambda k: prof[k][0])
+    r = roofline_family(fam, prof, n, m, K, stats, sm_mhz)
+    return r if r is not None else {"bound": "hbm", "kernel": fam, "achieved": None, "peak": None, "unit": "GB/s",
+                                    "frac": None, "traffic": None}
 
 
 def plain_leg(sb, m):
@@ -496,6 +575,69 @@ def batch_leg(args, P):
         "fr_min_median": float(np.median(cl["fr_min"])),
         "states_median": float(np.median(cl["n_states"])),
         "graphl_F_median": float(np.median(F_final.cpu().numpy())),
+    }
+    print(json.dumps(line), flush=True)
+    sb.close()
+    return 0
+
+
+def scale_leg(args, P):
+    """Paper-scale graphBpp: R-MAT with 2^24 vertex ids and 2^27 distinct
+    undirected edges, three planted factions (94.8 / 2.6 / 2.6 %, inter-faction
+    edges negative) with 15 % sign noise; each step grows 4096 trees (64
+    words), scores them and adds them to the cloud."""
+    import torch
+
+    n, u, v, s = args.scale_graph
+    sb = P.SignedBal(0)
+    t = time.perf_counter()
+    n1, m1, _ = sb.load_graph(n, u, v, s)
+    torch.cuda.synchronize()
+    ingest_s = time.perf_counter() - t
+    K = 4096
+    sb.cloud_reset(max_states=(args.warmup + args.steps) * K + 64)
+    counts = torch.empty(K, dtype=torch.int32, device="cuda")
+    hashes = torch.empty(K, dtype=torch.int64, device="cuda")
+
+    def step(i):
+        sb.sample_trees(SEED, i * K, K)
+        sb.frustration(counts, hashes)
+        return sb.cloud_insert()
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    sb.profile_read()
+    sb.profile(True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for i in range(args.steps):
+        step(args.warmup + i)
+    ev1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sb.profile(False)
+    prof = sb.profile_read()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    stats = sb.stats()
+    cl, fr_min = sb.cloud()
+    line = {
+        "leg": "scale24", "metric": "graphBpp edge-evals/s (trees x |E| / s), batched", "value": K * m1 / (ms / 1e3),
+        "unit": "edge-evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"rmat{args.scale}_3faction_K4096", "n": n1, "m": m1, "trees_per_step": K,
+                   "graph": f"R-MAT scale {args.scale}, 2^{args.edges_log2} undirected edges, three factions + "
+                            "15% sign noise, LCC",
+                   "generation_s": args.scale_gen_s, "ingest_s": ingest_s},
+        "gpu_launches": sum(c for _, c in prof.values()), "clocks": clk,
+        "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
+        "roofline": roofline(prof, n1, m1, K, stats, (clk or {}).get("sm_mhz")),
+        "roofline_score": roofline_family("score", prof, n1, m1, K),
+        "extras": {"fr_min": int(fr_min), "distinct_states": int(cl["S"].shape[0]), "bfs_stats": stats,
+                   "negative_fraction": float((s < 0).mean())},
     }
     print(json.dumps(line), flush=True)
     sb.close()

@@ -91,10 +91,67 @@ def rmat_two_faction(scale=20, m_target=1 << 24, noise=0.10, seed=1002):
     return n, u, v, sign
 
 
-def rmat_three_faction(scale=24, m_target=1 << 27, noise=0.15, probs=(0.948, 0.026, 0.026), seed=1003):
+RMAT_CHUNK = 1 << 22
+
+
+def _rmat_chunk_keys(a):
+    """One chunk of R-MAT draws as canonical pair keys (lo << 32 | hi), loops
+    dropped, duplicates inside the chunk dropped (first-seen order kept)."""
+    scale, k, abcd, seed, idx = a
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence(seed, spawn_key=(idx,))))
+    ta, tab, tabc = (int(round(x * 2**32)) for x in (abcd[0], abcd[0] + abcd[1], abcd[0] + abcd[1] + abcd[2]))
+    row = np.zeros(k, np.int64)
+    col = np.zeros(k, np.int64)
+    for _lvl in range(scale):
+        r = rng.integers(0, 1 << 32, k, dtype=np.uint64)
+        row <<= 1
+        row |= r >= tab
+        col <<= 1
+        col |= ((r >= ta) & (r < tab)) | (r >= tabc)
+    lo, hi = np.minimum(row, col), np.maximum(row, col)
+    key = ((lo << 32) | hi)[lo != hi]
+    _, first = np.unique(key, return_index=True)
+    first.sort()
+    return key[first]
+
+
+def rmat_edges_chunked(scale, m_target, abcd=(0.57, 0.19, 0.19, 0.05), seed=1003, workers=0):
+    """R-MAT drawn in fixed chunks of RMAT_CHUNK pairs, chunk i from its own
+    PCG64 stream (SeedSequence(seed, spawn_key=(i,))); the first m_target
+    distinct pairs in chunk order are kept, then a seeded vertex permutation.
+    The graph does not depend on `workers` (a spawned process pool)."""
+    n = 1 << scale
+    keys, have, nxt = [], 0, 0
+    while True:
+        nch = max(1, -(-int((m_target - have) * 1.15) // RMAT_CHUNK))
+        tasks = [(scale, RMAT_CHUNK, abcd, seed, nxt + i) for i in range(nch)]
+        nxt += nch
+        if workers > 0:
+            import concurrent.futures as cf
+            import multiprocessing as mp
+
+            with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+                keys.extend(ex.map(_rmat_chunk_keys, tasks))
+        else:
+            keys.extend(_rmat_chunk_keys(t) for t in tasks)
+        allk = np.concatenate(keys)
+        _, first = np.unique(allk, return_index=True)
+        have = first.shape[0]
+        if have >= m_target:
+            first.sort()
+            allk = allk[first[:m_target]]
+            break
+        keys = [allk[np.sort(first)]]
+    rng = _rng(seed)
+    perm = rng.permutation(n).astype(np.int32)
+    return n, perm[(allk >> 32).astype(np.int64)], perm[(allk & 0xFFFFFFFF).astype(np.int64)], rng
+
+
+def rmat_three_faction(scale=24, m_target=1 << 27, noise=0.15, probs=(0.948, 0.026, 0.026), seed=1003, workers=0):
     """Three factions (iid with `probs`), inter-faction edges negative,
-    intra-faction positive, then iid flips with probability `noise`."""
-    n, u, v, rng = rmat_edges(scale, m_target, seed=seed)
+    intra-faction positive, then iid flips with probability `noise`.  Edges
+    come from the chunked R-MAT draw (`workers` only changes the speed)."""
+    n, u, v, rng = rmat_edges_chunked(scale, m_target, seed=seed, workers=workers)
     fac = rng.choice(len(probs), size=n, p=np.asarray(probs) / np.sum(probs)).astype(np.int8)
     sign = np.where(fac[u] == fac[v], 1, -1).astype(np.int8)
     flip = rng.random(u.shape[0]) < noise
