@@ -508,11 +508,19 @@ __global__ void k_canon_out(const uint64_t* __restrict__ lab, int64_t total, int
 }
 
 // ------------------------------------------------------------------ scorer
-// S_t = sum over edges of bit t of lab[u] ^ lab[v] ^ neg.  Each thread owns
-// one word of a batch of <= 32 words and accumulates 64 vertical counters with
-// carry-save adders (ones, twos, fours) plus ripple planes for the eights.
+// S_t = sum over edges of bit t of lab[u] ^ lab[v] ^ neg.  The edge stream
+// (each edge from its colder to its hotter endpoint, sorted by the colder
+// one) moves through shared memory in tiles of SC_TILE edges, double-buffered
+// with bulk copies; a group of G lanes takes one edge at a time, lane = word
+// of 64 trees (two warps share an edge when there are more than 32 words),
+// and gathers the two label words.  Every lane keeps 64 vertical counters as
+// carry-save adders (ones, twos, fours) plus SC_PLANES ripple planes of
+// eights, flushed into 32-bit counts before the planes can overflow.
 #define SC_THREADS 256
-#define SC_PLANES 20
+#define SC_TILE 2048                     // edges per shared-memory tile (16 KB)
+#define SC_PLANES 12                     // ripple planes of the eights
+#define SC_FLUSH ((1 << SC_PLANES) - 1)  // batches of 8 edges between flushes
+#define SC_WAIT_CYCLES (4ll * 1000 * 1000 * 1000)  // ~2 s at 2 GHz
 
 __device__ __forceinline__ void csa(uint64_t& h, uint64_t& l, uint64_t a, uint64_t b, uint64_t c)
 {
@@ -521,73 +529,181 @@ __device__ __forceinline__ void csa(uint64_t& h, uint64_t& l, uint64_t a, uint64
     l = u ^ c;
 }
 
-template <int G>
-__global__ void __launch_bounds__(SC_THREADS) k_score(const int2* __restrict__ edges, int64_t m,
-                                                      const uint64_t* __restrict__ lab, int Wt, int w0, int Wb,
-                                                      uint32_t* __restrict__ counts)
-{
-    __shared__ uint32_t scnt[SB_WORDS_MAX * 64];
-    constexpr int NG = SC_THREADS / G;
-    const int tid = threadIdx.x;
-    const int gl = tid & (G - 1), grp = tid / G;
-    const bool act = gl < Wb;
-    for (int i = tid; i < Wb * 64; i += SC_THREADS) scnt[i] = 0;
-    __syncthreads();
-    const int64_t per = sb_cdiv(m, (int64_t)gridDim.x);
-    const int64_t e0 = (int64_t)blockIdx.x * per;
-    const int64_t e1 = min(m, e0 + per);
-    uint64_t ones = 0, twos = 0, fours = 0;
-    uint64_t P[SC_PLANES];
+struct ScoreArgs {
+    const int2* edges;    // m edges + 2 of padding: (colder, hotter | neg << 31)
+    int64_t m;
+    const uint64_t* lab;  // n x Wt label words
+    int Wt, w0, Wb;       // words [w0, w0 + Wb) of this launch, Wb <= 64
+    const int32_t* vgid;  // graph of every vertex (batches of graphs) or null
+    int64_t KP;           // count slots per graph
+    uint32_t* counts;     // [graph * KP + 64 * word + bit]
+    uint32_t* err;        // bit 0 set when a tile copy did not arrive in time
+};
+
+struct ScoreAcc {
+    uint64_t ones, twos, fours, P[SC_PLANES];
+    int nb;  // batches added since the last flush
+    __device__ __forceinline__ void reset()
+    {
+        ones = twos = fours = 0;
 #pragma unroll
-    for (int b = 0; b < SC_PLANES; b++) P[b] = 0;
-    const uint64_t* __restrict__ lw = lab + w0 + gl;
-    if (act) {
-        for (int64_t e = e0 + grp; e < e1; e += 8 * NG) {
-            uint64_t x[8];
+        for (int b = 0; b < SC_PLANES; b++) P[b] = 0;
+        nb = 0;
+    }
+    __device__ __forceinline__ void add8(const uint64_t* x)
+    {
+        uint64_t twosA, twosB, foursA, foursB, eights;
+        csa(twosA, ones, ones, x[0], x[1]);
+        csa(twosB, ones, ones, x[2], x[3]);
+        csa(foursA, twos, twos, twosA, twosB);
+        csa(twosA, ones, ones, x[4], x[5]);
+        csa(twosB, ones, ones, x[6], x[7]);
+        csa(foursB, twos, twos, twosA, twosB);
+        csa(eights, fours, fours, foursA, foursB);
+        uint64_t cy = eights;
 #pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const int64_t ee = e + (int64_t)k * NG;
-                x[k] = 0;
-                if (ee < e1) {
-                    const int2 ed = edges[ee];
-                    const uint32_t vv = (uint32_t)ed.y & SB_ID_MASK;
-                    const uint64_t negm = ed.y < 0 ? ~0ull : 0ull;
-                    x[k] = lw[(int64_t)ed.x * Wt] ^ lw[(int64_t)vv * Wt] ^ negm;
-                }
-            }
-            uint64_t twosA, twosB, foursA, foursB, eights;
-            csa(twosA, ones, ones, x[0], x[1]);
-            csa(twosB, ones, ones, x[2], x[3]);
-            csa(foursA, twos, twos, twosA, twosB);
-            csa(twosA, ones, ones, x[4], x[5]);
-            csa(twosB, ones, ones, x[6], x[7]);
-            csa(foursB, twos, twos, twosA, twosB);
-            csa(eights, fours, fours, foursA, foursB);
-            uint64_t cy = eights;
-#pragma unroll
-            for (int b = 0; b < SC_PLANES; b++) {
-                const uint64_t t = P[b] & cy;
-                P[b] ^= cy;
-                cy = t;
-            }
+        for (int b = 0; b < SC_PLANES; b++) {
+            const uint64_t t = P[b] & cy;
+            P[b] ^= cy;
+            cy = t;
         }
-        // each thread saw at most m / 8 groups of eights: < 2^SC_PLANES for m < 2^23 per block range
-#pragma unroll 1
+        nb++;
+    }
+    // adds the 64 counters into dst[0..63] (shared or global memory)
+    __device__ __forceinline__ void flush(uint32_t* dst)
+    {
+        if (nb == 0) return;
         for (int t = 0; t < 64; t++) {
             uint32_t hi = 0;
 #pragma unroll
             for (int b = 0; b < SC_PLANES; b++) hi |= (uint32_t)((P[b] >> t) & 1ull) << b;
             const uint32_t val = 8u * hi + 4u * (uint32_t)((fours >> t) & 1ull) + 2u * (uint32_t)((twos >> t) & 1ull) +
                                  (uint32_t)((ones >> t) & 1ull);
-            if (val) atomicAdd(&scnt[gl * 64 + t], val);
+            if (val) atomicAdd(dst + t, val);
         }
+        reset();
+    }
+};
+
+template <int G, bool SEG>
+__global__ void __launch_bounds__(SC_THREADS, SEG ? 3 : 4) k_score(ScoreArgs A)
+{
+    extern __shared__ __align__(128) unsigned char sc_smem[];
+    int2* tiles = (int2*)sc_smem;                        // 2 x SC_TILE edges
+    uint64_t* bar = (uint64_t*)(tiles + 2 * SC_TILE);    // 2 mbarriers
+    uint32_t* scnt = (uint32_t*)(bar + 2);               // Wb x 64 block counts (single graph)
+    __shared__ uint32_t s_fail;
+    constexpr int NG = SC_THREADS / G;
+    const int WS = (A.Wb + 31) >> 5;  // word slices of 32 (G == 32 when WS > 1)
+    const int tid = threadIdx.x, gl = tid & (G - 1), grp = tid / G;
+    const int slice = grp % WS, j = grp / WS, NGS = NG / WS;
+    const int word = slice * 32 + gl;
+    const bool act = word < A.Wb;
+    if (!SEG)
+        for (int i = tid; i < A.Wb * 64; i += SC_THREADS) scnt[i] = 0;
+    if (tid == 0) {
+        sb_mbar_init(&bar[0], 1);
+        sb_mbar_init(&bar[1], 1);
+        sb_mbar_init_fence();
+        s_fail = 0;
     }
     __syncthreads();
-    for (int i = tid; i < Wb * 64; i += SC_THREADS)
-        if (scnt[i]) atomicAdd(counts + 64 * w0 + i, scnt[i]);
+    const int64_t ntiles = sb_cdiv(A.m, SC_TILE);
+    const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+    // tile t -> buffer; the byte count is rounded up to 16 (the stream is padded)
+    auto issue = [&](int64_t t, int buf) {
+        const int64_t e0 = t * SC_TILE;
+        const int64_t cnt = min((int64_t)SC_TILE, A.m - e0);
+        sb_fence_proxy_async();
+        sb_bulk_load(tiles + buf * SC_TILE, A.edges + e0, (uint32_t)(((cnt + 1) & ~1ll) * sizeof(int2)), &bar[buf]);
+    };
+    if (tid == 0 && t0 < t1) issue(t0, 0);
+    const uint64_t* __restrict__ lw = A.lab + A.w0 + word;
+    const int Wt = A.Wt;
+    ScoreAcc acc;
+    acc.reset();
+    int64_t gcur = SEG ? -1 : 0;
+    uint32_t* const dst0 = SEG ? A.counts + 64 * (int64_t)(A.w0 + word) : scnt + 64 * word;
+    int64_t tf = -1;  // tile whose copy did not arrive
+    for (int64_t t = t0; t < t1; t++) {
+        const int buf = (int)((t - t0) & 1);
+        if (tid == 0 && t + 1 < t1) issue(t + 1, buf ^ 1);  // read by nobody since the last barrier
+        if (!sb_mbar_wait(&bar[buf], (uint32_t)(((t - t0) >> 1) & 1), SC_WAIT_CYCLES)) atomicOr(&s_fail, 1u);
+        __syncthreads();
+        if (s_fail) {
+            tf = t;
+            break;
+        }
+        const int2* te = tiles + buf * SC_TILE;
+        const int cnt = (int)min((int64_t)SC_TILE, A.m - t * SC_TILE);
+        if (act) {
+            for (int b = j; b < cnt; b += 8 * NGS) {
+                int2 ed[8];
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    const int i = b + k * NGS;
+                    ed[k] = i < cnt ? te[i] : make_int2(-1, 0);
+                }
+                uint64_t x[8];
+#pragma unroll
+                for (int k = 0; k < 8; k++)
+                    x[k] = ed[k].x >= 0 ? (lw[(int64_t)ed[k].x * Wt] ^ lw[(int64_t)((uint32_t)ed[k].y & SB_ID_MASK) * Wt] ^
+                                           (ed[k].y < 0 ? ~0ull : 0ull))
+                                        : 0ull;
+                if (SEG) {
+                    // edges are sorted by graph: split the batch into runs of one graph
+                    int32_t gk[8];
+                    uint32_t rem = 0;
+#pragma unroll
+                    for (int k = 0; k < 8; k++) {
+                        gk[k] = ed[k].x >= 0 ? A.vgid[ed[k].x] : -1;
+                        rem |= (ed[k].x >= 0 ? 1u : 0u) << k;
+                    }
+                    while (rem) {
+                        int32_t g = -1;
+#pragma unroll
+                        for (int k = 7; k >= 0; k--)
+                            if ((rem >> k) & 1u) g = gk[k];  // graph of the first remaining edge
+                        uint64_t xm[8];
+#pragma unroll
+                        for (int k = 0; k < 8; k++) {
+                            const bool tk = ((rem >> k) & 1u) && gk[k] == g;
+                            xm[k] = tk ? x[k] : 0ull;
+                            if (tk) rem &= ~(1u << k);
+                        }
+                        if (g != gcur) {
+                            if (gcur >= 0) acc.flush(dst0 + gcur * A.KP);
+                            gcur = g;
+                        }
+                        acc.add8(xm);
+                        if (acc.nb == SC_FLUSH) acc.flush(dst0 + gcur * A.KP);
+                    }
+                    continue;
+                } else {
+                    acc.add8(x);
+                }
+                if (acc.nb == SC_FLUSH) acc.flush(dst0 + gcur * A.KP);
+            }
+        }
+        __syncthreads();  // the buffer is reloaded by the next issue
+    }
+    if (s_fail) {
+        if (tid == 0) {
+            atomicOr(A.err, 1u);
+            // let the copies still in flight land (bounded) before the block exits
+            for (int64_t t = tf; t < min(tf + 2, t1); t++)
+                (void)sb_mbar_wait(&bar[(t - t0) & 1], (uint32_t)(((t - t0) >> 1) & 1), SC_WAIT_CYCLES);
+        }
+        return;
+    }
+    if (act && (!SEG || gcur >= 0)) acc.flush(dst0 + gcur * A.KP);
+    if (!SEG) {
+        __syncthreads();
+        for (int i = tid; i < A.Wb * 64; i += SC_THREADS)
+            if (scnt[i]) atomicAdd(A.counts + 64 * A.w0 + i, scnt[i]);
+    }
 }
 
-// per-launch counters are folded into the context after each launch
 __global__ void k_fold_stats(const uint32_t* sync, unsigned long long* acc)
 {
     const unsigned long long L = sync[7];
@@ -597,100 +713,6 @@ __global__ void k_fold_stats(const uint32_t* sync, unsigned long long* acc)
     acc[3] += *(const unsigned long long*)(sync + 10);
     acc[4] += *(const unsigned long long*)(sync + 12);
     acc[5] += *(const unsigned long long*)(sync + 14);
-}
-
-// Frustration counts of a batch of graphs: each group of lanes walks one
-// contiguous edge range; carry-save batches never cross a graph boundary, and
-// the counters are flushed (integer atomics) into counts[g * KP + tree] at
-// every boundary and at the end.
-template <int G>
-__global__ void __launch_bounds__(SC_THREADS) k_score_seg(const int2* __restrict__ edges, int64_t m,
-                                                          const uint64_t* __restrict__ lab, int Wt, int w0, int Wb,
-                                                          const int32_t* __restrict__ eoff, int64_t ngraphs,
-                                                          int64_t KP, uint32_t* __restrict__ counts)
-{
-    constexpr int NG = SC_THREADS / G;
-    const int tid = threadIdx.x;
-    const int gl = tid & (G - 1);
-    const bool act = gl < Wb;
-    const int64_t groups = (int64_t)gridDim.x * NG;
-    const int64_t gid = (int64_t)blockIdx.x * NG + tid / G;
-    const int64_t per = sb_cdiv(m, groups);
-    const int64_t e0 = gid * per, e1 = min(m, e0 + per);
-    if (!act || e0 >= e1) return;
-    const uint64_t* __restrict__ lw = lab + w0 + gl;
-    // graph of the first edge
-    int64_t g = 0;
-    {
-        int64_t lo = 0, hi = ngraphs - 1;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if ((int64_t)eoff[mid] <= e0) lo = mid;
-            else hi = mid - 1;
-        }
-        g = lo;
-    }
-    uint64_t ones = 0, twos = 0, fours = 0;
-    uint64_t P[SC_PLANES];
-#pragma unroll
-    for (int b = 0; b < SC_PLANES; b++) P[b] = 0;
-    int64_t e = e0;
-    while (e < e1) {
-        const int64_t gend = min(e1, (int64_t)eoff[g + 1]);
-        while (e < gend) {
-            uint64_t x[8];
-#pragma unroll
-            for (int k = 0; k < 8; k++) {
-                x[k] = 0;
-                if (e + k < gend) {
-                    const int2 ed = edges[e + k];
-                    const uint32_t vv = (uint32_t)ed.y & SB_ID_MASK;
-                    x[k] = lw[(int64_t)ed.x * Wt] ^ lw[(int64_t)vv * Wt] ^ (ed.y < 0 ? ~0ull : 0ull);
-                }
-            }
-            e = min(gend, e + 8);
-            uint64_t twosA, twosB, foursA, foursB, eights;
-            csa(twosA, ones, ones, x[0], x[1]);
-            csa(twosB, ones, ones, x[2], x[3]);
-            csa(foursA, twos, twos, twosA, twosB);
-            csa(twosA, ones, ones, x[4], x[5]);
-            csa(twosB, ones, ones, x[6], x[7]);
-            csa(foursB, twos, twos, twosA, twosB);
-            csa(eights, fours, fours, foursA, foursB);
-            uint64_t cy = eights;
-#pragma unroll
-            for (int b = 0; b < SC_PLANES; b++) {
-                const uint64_t t = P[b] & cy;
-                P[b] ^= cy;
-                cy = t;
-            }
-        }
-        // flush graph g
-        for (int t = 0; t < 64; t++) {
-            uint32_t hi = 0;
-#pragma unroll
-            for (int b = 0; b < SC_PLANES; b++) hi |= (uint32_t)((P[b] >> t) & 1ull) << b;
-            const uint32_t val = 8u * hi + 4u * (uint32_t)((fours >> t) & 1ull) + 2u * (uint32_t)((twos >> t) & 1ull) +
-                                 (uint32_t)((ones >> t) & 1ull);
-            if (val) atomicAdd(counts + g * KP + 64 * (w0 + gl) + t, val);
-        }
-        ones = twos = fours = 0;
-#pragma unroll
-        for (int b = 0; b < SC_PLANES; b++) P[b] = 0;
-        g++;
-    }
-}
-
-static const void* score_seg_kernel(int G)
-{
-    switch (G) {
-    case 1: return (const void*)k_score_seg<1>;
-    case 2: return (const void*)k_score_seg<2>;
-    case 4: return (const void*)k_score_seg<4>;
-    case 8: return (const void*)k_score_seg<8>;
-    case 16: return (const void*)k_score_seg<16>;
-    default: return (const void*)k_score_seg<32>;
-    }
 }
 
 // --------------------------------------------------------------- host side
@@ -714,15 +736,16 @@ static const void* bfs_kernel(int G)
     }
 }
 
+template <bool SEG>
 static const void* score_kernel(int G)
 {
     switch (G) {
-    case 1: return (const void*)k_score<1>;
-    case 2: return (const void*)k_score<2>;
-    case 4: return (const void*)k_score<4>;
-    case 8: return (const void*)k_score<8>;
-    case 16: return (const void*)k_score<16>;
-    default: return (const void*)k_score<32>;
+    case 1: return (const void*)k_score<1, SEG>;
+    case 2: return (const void*)k_score<2, SEG>;
+    case 4: return (const void*)k_score<4, SEG>;
+    case 8: return (const void*)k_score<8, SEG>;
+    case 16: return (const void*)k_score<16, SEG>;
+    default: return (const void*)k_score<32, SEG>;
     }
 }
 
@@ -881,57 +904,44 @@ extern "C" sb_status sb_sample_trees(sb_ctx* c, uint64_t seed, int64_t tree_begi
     return SB_OK;
 }
 
-// counts of the current batch (into c->counts), one pass per <= 32 words
+// counts of the current batch (into c->counts): one launch over all W <= 64 words
 sb_status sb_score_batch(sb_ctx* c)
 {
     if (c->counts_valid) return SB_OK;
     const int64_t ngraphs = c->batch_G > 0 ? c->batch_G : 1;
     SB_CHECK_CUDA(c, cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 64 * c->W * ngraphs, c->stream));
-    if (c->m > 0 && c->batch_G > 0) {
-        for (int w0 = 0; w0 < c->W; w0 += SB_WORDS_MAX) {
-            int Wb = c->W - w0 < SB_WORDS_MAX ? c->W - w0 : SB_WORDS_MAX;
-            int G = group_for(Wb);
-            const void* fn = score_seg_kernel(G);
-            int per_sm = 0;
-            SB_CHECK_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SC_THREADS, 0));
-            if (c->tune[SB_TUNE_SCORE_BLOCKS_SM] > 0) per_sm = std::min<int>(per_sm, (int)c->tune[SB_TUNE_SCORE_BLOCKS_SM]);
-            int64_t blocks = (int64_t)c->num_sms * (per_sm > 0 ? per_sm : 1);
-            int64_t min_blocks = sb_cdiv(c->m, (int64_t)(SC_THREADS / G) * 8 * ((1 << SC_PLANES) - 1));
-            if (blocks < min_blocks) blocks = min_blocks;
-            const int2* e = c->edges;
-            int64_t m = c->m;
-            const uint64_t* lab = c->labels;
-            int Wt = c->W;
-            const int32_t* eoff = c->b_eoff;
-            int64_t ng = c->batch_G;
-            int64_t KP = 64 * (int64_t)c->W;
-            uint32_t* cnt = (uint32_t*)c->counts;
-            void* args[] = {(void*)&e, &m, (void*)&lab, &Wt, &w0, &Wb, (void*)&eoff, &ng, &KP, &cnt};
-            SbProf prof(c, SB_PROF_SCORE);
-            SB_CHECK_CUDA(c, cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(SC_THREADS), args, 0, c->stream));
-            SB_TRY(sb_after_launch(c, "k_score_seg"));
-        }
-    } else if (c->m > 0) {
-        for (int w0 = 0; w0 < c->W; w0 += SB_WORDS_MAX) {
-            int Wb = c->W - w0 < SB_WORDS_MAX ? c->W - w0 : SB_WORDS_MAX;
-            int G = group_for(Wb);
-            const void* fn = score_kernel(G);
-            int per_sm = 0;
-            SB_CHECK_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SC_THREADS, 0));
-            int64_t blocks = (int64_t)c->num_sms * (per_sm > 0 ? per_sm : 1);
-            // every thread must see fewer than 8 * 2^SC_PLANES edges
-            int64_t min_blocks = sb_cdiv(c->m, (int64_t)(SC_THREADS / G) * 8 * ((1 << SC_PLANES) - 1));
-            if (blocks < min_blocks) blocks = min_blocks;
-            const int2* e = c->edges;
-            int64_t m = c->m;
-            const uint64_t* lab = c->labels;
-            int Wt = c->W;
-            uint32_t* cnt = (uint32_t*)c->counts;
-            void* args[] = {(void*)&e, &m, (void*)&lab, &Wt, &w0, &Wb, &cnt};
-            SbProf prof(c, SB_PROF_SCORE);
-            SB_CHECK_CUDA(c, cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(SC_THREADS), args, 0, c->stream));
-            SB_TRY(sb_after_launch(c, "k_score"));
-        }
+    if (c->m > 0) {
+        const bool seg = c->batch_G > 0;
+        const int Wb = c->W;
+        const int G = Wb >= 32 ? 32 : group_for(Wb);
+        const void* fn = seg ? score_kernel<true>(G) : score_kernel<false>(G);
+        const size_t smem = 2 * SC_TILE * sizeof(int2) + 2 * sizeof(uint64_t) + (seg ? 0 : sizeof(uint32_t) * 64 * Wb);
+        SB_CHECK_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        SB_CHECK_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SC_THREADS, smem));
+        if (c->tune[SB_TUNE_SCORE_BLOCKS_SM] > 0) per_sm = std::min<int>(per_sm, (int)c->tune[SB_TUNE_SCORE_BLOCKS_SM]);
+        const int64_t ntiles = sb_cdiv(c->m, SC_TILE);
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)c->num_sms * std::max(per_sm, 1), ntiles));
+        ScoreArgs A;
+        A.edges = c->sc_edges;
+        A.m = c->m;
+        A.lab = c->labels;
+        A.Wt = c->W;
+        A.w0 = 0;
+        A.Wb = Wb;
+        A.vgid = seg ? c->vgid : nullptr;
+        A.KP = 64 * (int64_t)c->W;
+        A.counts = (uint32_t*)c->counts;
+        A.err = c->sync + 28;
+        SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync + 28, 0, sizeof(uint32_t), c->stream));
+        void* args[] = {&A};
+        SbProf prof(c, SB_PROF_SCORE);
+        SB_CHECK_CUDA(c, cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(SC_THREADS), args, smem, c->stream));
+        SB_TRY(sb_after_launch(c, "k_score"));
+        uint32_t err = 0;
+        SB_CHECK_CUDA(c, cudaMemcpyAsync(&err, c->sync + 28, sizeof(err), cudaMemcpyDeviceToHost, c->stream));
+        SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (err) return sb_fail(c, SB_ERR_TIMEOUT, "scorer tile copy timed out");
     }
     c->counts_valid = true;
     return SB_OK;

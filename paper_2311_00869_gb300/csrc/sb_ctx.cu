@@ -233,6 +233,7 @@ void sb_release_graph(sb_ctx* c)
     sb_release_batch(c);
     sb_release_cloud(c);
     SB_FREE(edges);
+    SB_FREE(sc_edges);
     SB_FREE(rowptr);
     SB_FREE(col);
     SB_FREE(items);

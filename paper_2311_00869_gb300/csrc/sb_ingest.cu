@@ -488,6 +488,29 @@ struct BatchIn {
     const int64_t* eofs;
 };
 
+// key of the scorer's copy of an edge: (colder << (nb + 1)) | (hotter << 1) | neg,
+// colder = the endpoint of lower degree (on a tie, the larger id)
+__global__ void k_orient_keys(const int2* __restrict__ edges, int64_t m, const int32_t* __restrict__ deg, int nb,
+                              uint64_t* __restrict__ keys)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int2 ed = edges[e];
+        const uint32_t u = (uint32_t)ed.x, v = (uint32_t)ed.y & SB_ID_MASK;
+        const bool u_cold = deg[u] < deg[v];  // u < v, so a tie makes v the colder one
+        const uint64_t cold = u_cold ? u : v, hot = u_cold ? v : u;
+        keys[e] = (cold << (nb + 1)) | (hot << 1) | (uint64_t)(ed.y < 0 ? 1 : 0);
+    }
+}
+
+__global__ void k_emit_sc_edges(const uint64_t* __restrict__ keys, int64_t m, int nb, int2* __restrict__ out)
+{
+    const uint64_t idm = (1ull << nb) - 1ull;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = keys[e];
+        out[e] = make_int2((int32_t)(k >> (nb + 1)), (int32_t)((uint32_t)((k >> 1) & idm) | ((uint32_t)(k & 1ull) << 31)));
+    }
+}
+
 static sb_status load_graph_impl(sb_ctx* c, int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
                                  const int8_t* sign, uint32_t flags, int64_t* n_out, int64_t* m_out,
                                  int32_t* vmap_out, const BatchIn* B = nullptr)
@@ -650,6 +673,19 @@ static sb_status load_graph_impl(sb_ctx* c, int64_t n, int64_t m, const int32_t*
     SB_TRY(sb_scan_i32(c, low, lfirst, n1, nullptr));
     k_fill_lower<<<gm2, 256, 0, c->stream>>>(lkeys, m2, nb2, c->rowptr, lfirst, c->col);
     SB_TRY(sb_after_launch(c, "k_fill_lower"));
+    // scorer stream: every edge from its colder endpoint (lower degree) to
+    // the hotter one, sorted by (colder, hotter); two zero edges of padding
+    // let tile copies round their size up to 16 bytes
+    c->sc_edges = (int2*)sb_dalloc(c, sizeof(int2) * (size_t)(m2 + 2));
+    if (!c->sc_edges) return sb_fail(c, SB_ERR_OOM, "graph storage");
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->sc_edges + m2, 0, 2 * sizeof(int2), c->stream));
+    if (m2 > 0) {
+        k_orient_keys<<<gm2, 256, 0, c->stream>>>(c->edges, m2, deg, nb2, lkeys);
+        SB_TRY(sb_after_launch(c, "k_orient_keys"));
+        SB_TRY(sb_radix_sort_u64(c, lkeys, m2, 2 * nb2 + 1));
+        k_emit_sc_edges<<<gm2, 256, 0, c->stream>>>(lkeys, m2, nb2, c->sc_edges);
+        SB_TRY(sb_after_launch(c, "k_emit_sc_edges"));
+    }
     if (B) {
         const int64_t G = B->G;
         c->b_voff = (int32_t*)sb_dalloc(c, sizeof(int32_t) * (size_t)(G + 1));

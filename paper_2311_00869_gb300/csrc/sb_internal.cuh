@@ -92,6 +92,7 @@ struct sb_ctx {
     bool has_graph = false;
     int64_t n = 0, m = 0;
     int2* edges = nullptr;        // m: (u, v | neg << 31), u < v, lexicographic
+    int2* sc_edges = nullptr;     // m + 2: (colder, hotter | neg << 31) by (colder, hotter); scorer stream
     int32_t* rowptr = nullptr;    // n + 1
     int32_t* col = nullptr;       // 2m: neighbour | neg << 31
     sb_bfs_item* items = nullptr; // BFS work items
@@ -248,3 +249,51 @@ sb_status sb_score_batch(sb_ctx* c);
 __host__ __device__ __forceinline__ int64_t sb_cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 __device__ __forceinline__ unsigned sb_lane() { return threadIdx.x & 31u; }
+
+// ---------------------------------------------------------------- TMA (bulk)
+// One-dimensional bulk copies global -> shared (cp.async.bulk) completing on
+// an mbarrier.  Source and destination 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ uint32_t sb_smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void sb_mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sb_smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void sb_mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void sb_fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void sb_bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sb_smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     sb_smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(sb_smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool sb_mbar_test(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(sb_smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for phase `parity` of `bar` for at most `limit` cycles; false on timeout.
+__device__ __forceinline__ bool sb_mbar_wait(uint64_t* bar, uint32_t parity, long long limit)
+{
+    if (sb_mbar_test(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!sb_mbar_test(bar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
