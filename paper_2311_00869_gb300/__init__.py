@@ -260,7 +260,7 @@ class SignedBal:
     def sync(self):
         self._check(self.lib.sb_sync(self.h))
 
-    TUNE_KNOBS = {"bfs_words": 0, "score_blocks_sm": 1, "gl_lanes": 2}
+    TUNE_KNOBS = {"bfs_words": 0, "score_blocks_sm": 1, "gl_lanes": 2, "bfs_group": 3}
 
     def set_tuning(self, **knobs):
         for k, v in knobs.items():

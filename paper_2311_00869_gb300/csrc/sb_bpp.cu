@@ -22,6 +22,12 @@
 #define BFS_THREADS_PAR 128
 #define BFS_QUEUE_PER_LANE 32  // candidate-queue entries per lane (overflow falls back to per-lane hashing)
 #define SYNC_WORDS 32
+// Shared-memory slots of (owner thread o, tree t): owner-major rows padded so
+// that one owner's trees, and one tree of consecutive owners, fall in
+// different banks (the hash rounds walk one owner's trees in lockstep).
+#define BSLOT(o, t) ((o) * 65 + (t))  // 32-bit minima / winner ids
+#define LSLOT(o, t) ((o) * 68 + (t))  // winner label bytes
+#define KSLOT(w, t) ((w) * 65 + (t))  // tree salts of word w
 #define BAR_LIMIT_CYCLES (4ll * 1000 * 1000 * 1000)  // ~2 s at 2 GHz
 
 struct BfsArgs {
@@ -103,15 +109,17 @@ __device__ __forceinline__ int group_excl_scan(int x, unsigned gmask, int gl, in
 //   HASH = false: once / twice = trees reached through >= 1 / >= 2 candidates,
 //                 labx = candidate label bits (exact where once & ~twice).
 //   HASH = true : running argmin of the hashed parent key over the candidates
-//                 in `mask`.  For each neighbour the group's candidate bits are
-//                 first compacted into a shared queue (entry = owner lane,
-//                 tree, label bit), then hashed by all lanes of the group in
-//                 lockstep; a neighbour contributes at most one entry per
-//                 (word, tree), so the slot updates of one round never collide.
-//                 best[slot] (initialised to 0xFFFFFFFF) holds the smallest
-//                 hash, labb / bestu the winner's label bit / id; keys are
-//                 distinct (the hash is a bijection in u), so `h <= best`
-//                 accepts exactly the minimum.  `once` returns the trees seen.
+//                 in `mask`.  The group's candidate bits are compacted into a
+//                 shared queue (entry = neighbour, owner lane, tree, label
+//                 bit) and hashed by all lanes of the group in lockstep: the
+//                 8 neighbours of a tile at once (atomicMin, then the entry
+//                 equal to the minimum writes its label), or, when they hold
+//                 more candidates than the queue, one neighbour at a time (its
+//                 entries have distinct slots).  best (initialised to
+//                 0xFFFFFFFF) holds the smallest hash, labb / bestu the
+//                 winner's label bit / id; keys are distinct (the hash is a
+//                 bijection in u), so `h <= best` accepts exactly the minimum.
+//                 `once` returns the trees seen.
 // `cur` and `lab` are rewritten between levels by other blocks, so they are
 // read with plain (coherent) loads; the column array is read-only.
 template <bool HASH, bool PAR, int BD, int G>
@@ -141,28 +149,79 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
             }
         } else {
             const int owner0 = tid - gl;  // thread index of the group's lane 0
+            int cnt = 0;
 #pragma unroll
             for (int k = 0; k < 8; k++) {
                 once |= f[k];
-                const int cnt = __popcll(f[k]);
-                int T;
-                int pos = group_excl_scan<G>(cnt, gmask, gl, T);
-                if (T == 0) continue;  // same for the whole group
-                nhash += (uint32_t)cnt;
-                const uint32_t u = (c[k] & SB_ID_MASK) - goff;  // id inside the graph
-                const uint32_t hx = u ^ y;
-                if (T > BFS_QUEUE_PER_LANE * G) {
-                    // rare: more candidates than the queue holds; each lane
-                    // hashes its own bits (it alone owns their slots)
+                cnt += __popcll(f[k]);
+            }
+            int T;
+            int pos = group_excl_scan<G>(cnt, gmask, gl, T);
+            if (T == 0) continue;  // same for the whole group
+            nhash += (uint32_t)cnt;
+            if (T <= BFS_QUEUE_PER_LANE * G) {
+                // the candidates of all 8 neighbours go through one queue of
+                // (neighbour, owner word, tree, label bit) entries; lanes hash
+                // them in lockstep, keep each tree's minimum with atomicMin
+                // (two neighbours may reach the same tree) and then let the
+                // one entry equal to the minimum write its label bit
+#pragma unroll
+                for (int k = 0; k < 8; k++)
                     for (uint64_t b = f[k]; b;) {
                         const int t = __ffsll((long long)b) - 1;
                         b &= b - 1;
-                        const uint32_t h = sb_fmix32(hx + akey[gl * 64 + t]);
-                        const int slot = t * BD + tid;
-                        if (h <= best[slot]) {
-                            best[slot] = h;
-                            labb[slot] = (uint8_t)((l[k] >> t) & 1ull);
-                            if (PAR) bestu[slot] = (int32_t)u;
+                        queue[pos++] = (uint16_t)((k << 12) | (gl << 7) | (t << 1) | (int)((l[k] >> t) & 1ull));
+                    }
+                __syncwarp(gmask);
+                for (int i = gl; i < T; i += G) {
+                    const uint32_t e = queue[i];
+                    const int k = (int)(e >> 12), ow = (int)((e >> 7) & 31u), t = (int)((e >> 1) & 63u);
+                    uint32_t ck = c[0];
+#pragma unroll
+                    for (int q = 1; q < 8; q++)
+                        if (k == q) ck = c[q];
+                    const uint32_t h = sb_fmix32((((ck & SB_ID_MASK) - goff) ^ y) + akey[KSLOT(ow, t)]);
+                    atomicMin(&best[BSLOT(owner0 + ow, t)], h);
+                }
+                __syncwarp(gmask);
+                for (int i = gl; i < T; i += G) {
+                    const uint32_t e = queue[i];
+                    const int k = (int)(e >> 12), ow = (int)((e >> 7) & 31u), t = (int)((e >> 1) & 63u);
+                    uint32_t ck = c[0];
+#pragma unroll
+                    for (int q = 1; q < 8; q++)
+                        if (k == q) ck = c[q];
+                    const uint32_t u = (ck & SB_ID_MASK) - goff;
+                    const uint32_t h = sb_fmix32((u ^ y) + akey[KSLOT(ow, t)]);
+                    const int o = owner0 + ow;
+                    if (best[BSLOT(o, t)] == h) {  // fmix32 is injective in u: one entry matches
+                        labb[LSLOT(o, t)] = (uint8_t)(e & 1u);
+                        if (PAR) bestu[BSLOT(o, t)] = (int32_t)u;
+                    }
+                }
+                __syncwarp(gmask);
+                continue;
+            }
+            // many candidates: one neighbour at a time
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int cntk = __popcll(f[k]);
+                int Tk;
+                int posk = group_excl_scan<G>(cntk, gmask, gl, Tk);
+                if (Tk == 0) continue;  // same for the whole group
+                const uint32_t u = (c[k] & SB_ID_MASK) - goff;  // id inside the graph
+                const uint32_t hx = u ^ y;
+                if (Tk > BFS_QUEUE_PER_LANE * G) {
+                    // more candidates than the queue holds; each lane hashes
+                    // its own bits (it alone owns their slots)
+                    for (uint64_t b = f[k]; b;) {
+                        const int t = __ffsll((long long)b) - 1;
+                        b &= b - 1;
+                        const uint32_t h = sb_fmix32(hx + akey[KSLOT(gl, t)]);
+                        if (h <= best[BSLOT(tid, t)]) {  // <=: the minima start at 0xFFFFFFFF
+                            best[BSLOT(tid, t)] = h;
+                            labb[LSLOT(tid, t)] = (uint8_t)((l[k] >> t) & 1ull);
+                            if (PAR) bestu[BSLOT(tid, t)] = (int32_t)u;
                         }
                     }
                     __syncwarp(gmask);
@@ -171,18 +230,29 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
                 for (uint64_t b = f[k]; b;) {
                     const int t = __ffsll((long long)b) - 1;
                     b &= b - 1;
-                    queue[pos++] = (uint16_t)((gl << 7) | (t << 1) | (int)((l[k] >> t) & 1ull));
+                    queue[posk++] = (uint16_t)((gl << 7) | (t << 1) | (int)((l[k] >> t) & 1ull));
                 }
                 __syncwarp(gmask);
-                for (int i = gl; i < T; i += G) {
-                    const uint32_t e = queue[i];
-                    const int ow = (int)(e >> 7), t = (int)((e >> 1) & 63u);
-                    const uint32_t h = sb_fmix32(hx + akey[ow * 64 + t]);
-                    const int slot = t * BD + owner0 + ow;
-                    if (h <= best[slot]) {
-                        best[slot] = h;
-                        labb[slot] = (uint8_t)(e & 1u);
-                        if (PAR) bestu[slot] = (int32_t)u;
+                // two entries per lane and round: entries of one neighbour have
+                // distinct slots, so their updates are independent
+                for (int i = gl; i < Tk; i += 2 * G) {
+                    const bool two = i + G < Tk;
+                    const uint32_t ea = queue[i], eb = queue[two ? i + G : i];
+                    const int owa = (int)((ea >> 7) & 31u), ta = (int)((ea >> 1) & 63u);
+                    const int owb = (int)((eb >> 7) & 31u), tb = (int)((eb >> 1) & 63u);
+                    const uint32_t ha = sb_fmix32(hx + akey[KSLOT(owa, ta)]);
+                    const uint32_t hb = sb_fmix32(hx + akey[KSLOT(owb, tb)]);
+                    const int oa = owner0 + owa, ob = owner0 + owb;
+                    const uint32_t ba = best[BSLOT(oa, ta)], bb = best[BSLOT(ob, tb)];
+                    if (ha <= ba) {
+                        best[BSLOT(oa, ta)] = ha;
+                        labb[LSLOT(oa, ta)] = (uint8_t)(ea & 1u);
+                        if (PAR) bestu[BSLOT(oa, ta)] = (int32_t)u;
+                    }
+                    if (two && hb <= bb) {
+                        best[BSLOT(ob, tb)] = hb;
+                        labb[LSLOT(ob, tb)] = (uint8_t)(eb & 1u);
+                        if (PAR) bestu[BSLOT(ob, tb)] = (int32_t)u;
                     }
                 }
                 __syncwarp(gmask);
@@ -199,7 +269,7 @@ __device__ __forceinline__ void best_reset(uint32_t* best, int tid, uint64_t mas
     for (uint64_t b = mask; b;) {
         const int t = __ffsll((long long)b) - 1;
         b &= b - 1;
-        best[t * BD + tid] = 0xFFFFFFFFu;
+        best[BSLOT(tid, t)] = 0xFFFFFFFFu;
     }
 }
 
@@ -210,22 +280,22 @@ __device__ __forceinline__ uint64_t winner_labels(const uint8_t* labb, int tid, 
     for (uint64_t b = mask; b;) {
         const int t = __ffsll((long long)b) - 1;
         b &= b - 1;
-        lx |= (uint64_t)labb[t * BD + tid] << t;
+        lx |= (uint64_t)labb[LSLOT(tid, t)] << t;
     }
     return lx;
 }
 
 template <int G, bool PAR>
-__global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
+__global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
     k_bfs(BfsArgs A)
 {
     constexpr int BD = PAR ? BFS_THREADS_PAR : BFS_THREADS;
     extern __shared__ uint32_t smem[];
-    uint32_t* akey = smem;                        // Wb * 64 tree salts
-    uint32_t* best = smem + A.Wb * 64;            // 64 x BD running minima
-    uint8_t* labb = (uint8_t*)(best + 64 * BD);   // 64 x BD winners' label bits
-    uint16_t* queues = (uint16_t*)(labb + 64 * BD);  // BFS_QUEUE_PER_LANE x G entries per group
-    int32_t* bestu = (int32_t*)(queues + BFS_QUEUE_PER_LANE * BD);  // 64 x BD winners (PAR only)
+    uint32_t* akey = smem;                        // tree salts, KSLOT(word, tree)
+    uint32_t* best = smem + A.Wb * 65;            // running minima, BSLOT(thread, tree)
+    uint8_t* labb = (uint8_t*)(best + 65 * BD);   // winners' label bits, LSLOT(thread, tree)
+    uint16_t* queues = (uint16_t*)(labb + 68 * BD);  // BFS_QUEUE_PER_LANE x G entries per group
+    int32_t* bestu = (int32_t*)(queues + BFS_QUEUE_PER_LANE * BD);  // winners, BSLOT (PAR only)
     __shared__ uint32_t s_any, s_stop;
 
     const int tid = threadIdx.x;
@@ -236,7 +306,8 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
     const int64_t group_id = (int64_t)blockIdx.x * (BD / G) + tid / G;
     const unsigned nblocks = gridDim.x;
 
-    for (int i = tid; i < A.Wb * 64; i += BD) akey[i] = (uint32_t)sb_tree_key(A.S, A.tree0 + 64 * (int64_t)A.w0 + i);
+    for (int i = tid; i < A.Wb * 64; i += BD)
+        akey[KSLOT(i >> 6, i & 63)] = (uint32_t)sb_tree_key(A.S, A.tree0 + 64 * (int64_t)A.w0 + i);
     if (tid == 0) s_any = 0;
     __syncthreads();
 
@@ -251,80 +322,88 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS)
         bool any_new = false;
 
         // ---- phase A: every work item (whole rows, and chunks of split rows)
-        for (int64_t it = group_id; it < A.n_items; it += groups_total) {
-            const sb_bfs_item itm = A.items[it];
-            const int32_t v = itm.v;
-            const int32_t d = A.done[v];
-            if (d >= 0 && L >= d + 3) continue;
-            const uint64_t vis_w = act ? A.vis[(int64_t)v * Wb + gl] : ~0ull;
-            const uint64_t U = ~vis_w;
-            const int32_t* cp = A.col + itm.beg;
-            const int len = itm.end - itm.beg;
-            const bool hub = itm.hub >= 0;
-            uint64_t once = 0, twice = 0, labx = 0;
-            // the passes below synchronise the group's lanes, so every lane of
-            // the group enters them (a lane with nothing to do has mask 0)
-            if (__any_sync(gmask, U != 0)) {
-                const uint32_t goff = A.vgoff ? (uint32_t)A.vgoff[v] : 0u;
-                const uint32_t y = sb_child_salt(A.S, (uint32_t)v - goff);
-                if (U) n_scan += (uint32_t)len;
-                if (!hub && !PAR) {
-                    scan_row<false, PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, goff, akey, best, labb,
-                                                bestu, queue, tid, gmask, once, twice, labx, n_hash);
-                    if (__any_sync(gmask, twice != 0)) {
-                        // trees reached through two or more candidates: hashed argmin
-                        uint64_t o2 = 0, t2 = 0, l2 = 0;
-                        if (twice) n_pass2 += (uint32_t)len;
-                        best_reset<BD>(best, tid, twice);
-                        scan_row<true, PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, twice, y, goff, akey, best,
-                                                   labb, bestu, queue, tid, gmask, o2, t2, l2, n_hash);
-                        labx = (labx & ~twice) | (winner_labels<BD>(labb, tid, twice) & twice);
+        // The items are sorted by descending degree and dealt out in rounds of
+        // one item per group, the order of the groups reversing every round,
+        // so that every group's sum of item sizes comes out about the same.
+        for (int64_t r = 0;; r++) {
+            const int64_t it_beg = r * groups_total + ((r & 1) ? groups_total - 1 - group_id : group_id);
+            if (r * groups_total >= A.n_items) break;
+            const int64_t it_end = min(A.n_items, it_beg + 1);
+            for (int64_t it = it_beg; it < it_end; it++) {
+                const sb_bfs_item itm = A.items[it];
+                const int32_t v = itm.v;
+                const int32_t d = A.done[v];
+                if (d >= 0 && L >= d + 3) continue;
+                const uint64_t vis_w = act ? A.vis[(int64_t)v * Wb + gl] : ~0ull;
+                const uint64_t U = ~vis_w;
+                const int32_t* cp = A.col + itm.beg;
+                const int len = itm.end - itm.beg;
+                const bool hub = itm.hub >= 0;
+                uint64_t once = 0, twice = 0, labx = 0;
+                // the passes below synchronise the group's lanes, so every lane of
+                // the group enters them (a lane with nothing to do has mask 0)
+                if (__any_sync(gmask, U != 0)) {
+                    const uint32_t goff = A.vgoff ? (uint32_t)A.vgoff[v] : 0u;
+                    const uint32_t y = sb_child_salt(A.S, (uint32_t)v - goff);
+                    if (U) n_scan += (uint32_t)len;
+                    if (!hub && !PAR) {
+                        scan_row<false, PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, goff, akey, best, labb,
+                                                    bestu, queue, tid, gmask, once, twice, labx, n_hash);
+                        if (__any_sync(gmask, twice != 0)) {
+                            // trees reached through two or more candidates: hashed argmin
+                            uint64_t o2 = 0, t2 = 0, l2 = 0;
+                            if (twice) n_pass2 += (uint32_t)len;
+                            best_reset<BD>(best, tid, twice);
+                            scan_row<true, PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, twice, y, goff, akey, best,
+                                                       labb, bestu, queue, tid, gmask, o2, t2, l2, n_hash);
+                            labx = (labx & ~twice) | (winner_labels<BD>(labb, tid, twice) & twice);
+                        }
+                    } else {
+                        best_reset<BD>(best, tid, U);
+                        scan_row<true, PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, goff, akey, best, labb,
+                                                   bestu, queue, tid, gmask, once, twice, labx,
+                                                   hub ? n_hash_hub : n_hash);
+                        labx = winner_labels<BD>(labb, tid, once);
                     }
-                } else {
-                    best_reset<BD>(best, tid, U);
-                    scan_row<true, PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, goff, akey, best, labb,
-                                               bestu, queue, tid, gmask, once, twice, labx,
-                                               hub ? n_hash_hub : n_hash);
-                    labx = winner_labels<BD>(labb, tid, once);
                 }
-            }
-            if (hub) {
-                // chunk of a split row: publish the chunk minima, one atomic per tree
-                if (once) {
-                    uint64_t* hb = A.hubbest + ((int64_t)itm.hub * Wb + gl) * 64;
+                if (hub) {
+                    // chunk of a split row: publish the chunk minima, one atomic per tree
+                    if (once) {
+                        uint64_t* hb = A.hubbest + ((int64_t)itm.hub * Wb + gl) * 64;
+                        for (uint64_t b = once; b;) {
+                            const int t = __ffsll((long long)b) - 1;
+                            b &= b - 1;
+                            const unsigned long long key = ((unsigned long long)best[BSLOT(tid, t)] << 32) |
+                                                           (PAR ? ((unsigned long long)(uint32_t)bestu[BSLOT(tid, t)] << 1) : 0ull) |
+                                                           ((labx >> t) & 1ull);
+                            atomicMin((unsigned long long*)(hb + t), key);
+                        }
+                        atomicOr((unsigned long long*)(A.hubnew + (int64_t)itm.hub * Wb + gl), once);
+                    }
+                    continue;
+                }
+                if (PAR && A.parents) {
                     for (uint64_t b = once; b;) {
                         const int t = __ffsll((long long)b) - 1;
                         b &= b - 1;
-                        const unsigned long long key = ((unsigned long long)best[t * BD + tid] << 32) |
-                                                       (PAR ? ((unsigned long long)(uint32_t)bestu[t * BD + tid] << 1) : 0ull) |
-                                                       ((labx >> t) & 1ull);
-                        atomicMin((unsigned long long*)(hb + t), key);
+                        A.parents[(64 * (int64_t)wofs + t) * A.n + v] = bestu[BSLOT(tid, t)];
                     }
-                    atomicOr((unsigned long long*)(A.hubnew + (int64_t)itm.hub * Wb + gl), once);
                 }
-                continue;
-            }
-            if (PAR && A.parents) {
-                for (uint64_t b = once; b;) {
-                    const int t = __ffsll((long long)b) - 1;
-                    b &= b - 1;
-                    A.parents[(64 * (int64_t)wofs + t) * A.n + v] = bestu[t * BD + tid];
+                if (act) {
+                    if (once) {
+                        A.lab[(int64_t)v * Wt + wofs] |= labx & once;
+                        A.vis[(int64_t)v * Wb + gl] = vis_w | once;
+                        any_new = true;
+                    }
+                    nxt[(int64_t)v * Wb + gl] = once;
+                }
+                if (d < 0) {
+                    const bool full = (vis_w | once) == ~0ull;
+                    const bool all = __all_sync(gmask, full);
+                    if (all && gl == 0) A.done[v] = L;
                 }
             }
-            if (act) {
-                if (once) {
-                    A.lab[(int64_t)v * Wt + wofs] |= labx & once;
-                    A.vis[(int64_t)v * Wb + gl] = vis_w | once;
-                    any_new = true;
-                }
-                nxt[(int64_t)v * Wb + gl] = once;
-            }
-            if (d < 0) {
-                const bool full = (vis_w | once) == ~0ull;
-                const bool all = __all_sync(gmask, full);
-                if (all && gl == 0) A.done[v] = L;
-            }
-        }
+        }  // rounds
 
         // ---- phase B: resolve split rows
         if (A.n_hubs > 0) {
@@ -761,11 +840,13 @@ static sb_status ensure_sync(sb_ctx* c)
 static sb_status run_bfs(sb_ctx* c, int w0, int Wb, int32_t* parents)
 {
     const bool par = parents != nullptr;
-    const int G = group_for(Wb);
+    // lanes beyond the launch's words still share the hash rounds
+    const int Gw = group_for(Wb), Gt = (int)c->tune[SB_TUNE_BFS_GROUP];
+    const int G = (Gt > Gw && Gt <= 2 * Gw) ? Gt : Gw;  // widened at most twofold
     const int BD = par ? BFS_THREADS_PAR : BFS_THREADS;
     const void* fn = par ? bfs_kernel<true>(G) : bfs_kernel<false>(G);
-    size_t smem = sizeof(uint32_t) * ((size_t)Wb * 64 + 64 * BD) + 64 * BD + sizeof(uint16_t) * BFS_QUEUE_PER_LANE * BD +
-                  (par ? sizeof(int32_t) * 64 * BD : 0);
+    size_t smem = sizeof(uint32_t) * ((size_t)Wb * 65 + 65 * BD) + 68 * BD + sizeof(uint16_t) * BFS_QUEUE_PER_LANE * BD +
+                  (par ? sizeof(int32_t) * 65 * BD : 0);
     SB_CHECK_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     SB_CHECK_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BD, smem));

@@ -320,6 +320,8 @@ extern "C" sb_status sb_set_tuning(sb_ctx* c, int32_t knob, int64_t value)
     if (knob == SB_TUNE_SCORE_BLOCKS_SM && value > 32) return sb_fail(c, SB_ERR_ARG, "at most 32 blocks per SM");
     if (knob == SB_TUNE_GL_LANES && value != 0 && value != 8 && value != 32)
         return sb_fail(c, SB_ERR_ARG, "graphL lanes must be 8 or 32");
+    if (knob == SB_TUNE_BFS_GROUP && (value > 32 || (value & (value - 1)) != 0))
+        return sb_fail(c, SB_ERR_ARG, "BFS group must be a power of two <= 32");
     c->tune[knob] = value;
     return SB_OK;
 }

@@ -169,7 +169,36 @@ __global__ void __launch_bounds__(GL_THREADS) k_gl_rows(GlArgs A)
                 for (int jj = 0; jj < cnt; jj += SL) {
                     const int cc_n = min(SL, cnt - jj);
                     const uint32_t mycol = sl < cc_n ? (uint32_t)__ldg(A.col + j0 + jj + sl) : 0u;
-                    for (int q = 0; q < cc_n; q++) {
+                    int q0 = 0;
+                    if constexpr (VEC == 4) {
+                        // four neighbour rows in flight, then added in order
+                        for (; q0 + 4 <= cc_n; q0 += 4) {
+                            uint32_t cc[4];
+                            float4 x[4];
+#pragma unroll
+                            for (int i = 0; i < 4; i++) cc[i] = __shfl_sync(smask, mycol, q0 + i, SL);
+                            if (act) {
+#pragma unroll
+                                for (int i = 0; i < 4; i++)
+                                    x[i] = Vec<4>::ld(A.gin + (int64_t)(cc[i] & SB_ID_MASK) * R + r0);
+#pragma unroll
+                                for (int i = 0; i < 4; i++) {
+                                    const uint32_t nb = cc[i] & 0x80000000u, nb1 = cc[i] >> 31;
+                                    blk[0] += flip_sign(x[i].x, nb);
+                                    blk[1 % VEC] += flip_sign(x[i].y, nb);
+                                    blk[2 % VEC] += flip_sign(x[i].z, nb);
+                                    blk[3 % VEC] += flip_sign(x[i].w, nb);
+                                    if (wantF) {
+                                        fcnt[0] += (int)(is_neg(x[i].x) ^ nb1 ^ sv[0]);
+                                        fcnt[1 % VEC] += (int)(is_neg(x[i].y) ^ nb1 ^ sv[1 % VEC]);
+                                        fcnt[2 % VEC] += (int)(is_neg(x[i].z) ^ nb1 ^ sv[2 % VEC]);
+                                        fcnt[3 % VEC] += (int)(is_neg(x[i].w) ^ nb1 ^ sv[3 % VEC]);
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    for (int q = q0; q < cc_n; q++) {
                         const uint32_t cc = __shfl_sync(smask, mycol, q, SL);
                         const uint32_t nb = cc & 0x80000000u;
                         const uint32_t nb1 = cc >> 31;

@@ -178,7 +178,7 @@ struct sb_ctx {
     size_t tmp_cap = 0;
 
     // tuning knobs (SB_TUNE_*)
-    int64_t tune[SB_TUNE_N] = {0, 0, 0};
+    int64_t tune[SB_TUNE_N] = {0, 0, 0, 0};
 
     // profiling: per-family launch counts, optional CUDA-event timing
     int prof_on = 0;
