@@ -155,10 +155,42 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
                 once |= f[k];
                 cnt += __popcll(f[k]);
             }
+            const unsigned Tsum = __reduce_add_sync(gmask, (unsigned)cnt);
+            if (Tsum == 0) continue;  // same for the whole group
+            nhash += (uint32_t)cnt;
+            const unsigned cmax = __reduce_max_sync(gmask, (unsigned)cnt);
+            if (cmax * G <= 2 * Tsum + 2 * G) {
+                // the lanes' shares are even enough: every lane hashes its own
+                // candidates into its own slots, two at a time, no queue
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    const uint32_t u = (c[k] & SB_ID_MASK) - goff;
+                    const uint32_t hx = u ^ y;
+                    for (uint64_t b = f[k]; b;) {
+                        const int ta = __ffsll((long long)b) - 1;
+                        b &= b - 1;
+                        const int tb = b ? __ffsll((long long)b) - 1 : ta;
+                        const bool two = b != 0;
+                        b &= b - 1;
+                        const uint32_t ha = sb_fmix32(hx + akey[KSLOT(gl, ta)]);
+                        const uint32_t hb = sb_fmix32(hx + akey[KSLOT(gl, tb)]);
+                        const uint32_t ba = best[BSLOT(tid, ta)], bb = best[BSLOT(tid, tb)];
+                        if (ha <= ba) {  // <=: the minima start at 0xFFFFFFFF
+                            best[BSLOT(tid, ta)] = ha;
+                            labb[LSLOT(tid, ta)] = (uint8_t)((l[k] >> ta) & 1ull);
+                            if (PAR) bestu[BSLOT(tid, ta)] = (int32_t)u;
+                        }
+                        if (two && hb <= bb) {
+                            best[BSLOT(tid, tb)] = hb;
+                            labb[LSLOT(tid, tb)] = (uint8_t)((l[k] >> tb) & 1ull);
+                            if (PAR) bestu[BSLOT(tid, tb)] = (int32_t)u;
+                        }
+                    }
+                }
+                continue;
+            }
             int T;
             int pos = group_excl_scan<G>(cnt, gmask, gl, T);
-            if (T == 0) continue;  // same for the whole group
-            nhash += (uint32_t)cnt;
             if (T <= BFS_QUEUE_PER_LANE * G) {
                 // the candidates of all 8 neighbours go through one queue of
                 // (neighbour, owner word, tree, label bit) entries; lanes hash
