@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--gl-steps", type=int, default=500, help="graphL descent steps (--leg graphl)")
     ap.add_argument("--graphs", type=int, default=4096, help="graphs in the uneven batch (--leg batch)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default tuning knobs")
+    ap.add_argument("--gl-lanes", type=int, default=0, help="graphL lanes per row segment (8 or 32; with --no-tune)")
     args = ap.parse_args()
     big = args.leg == "scale24"
     args.scale = args.scale if args.scale is not None else (24 if big else 20)
@@ -241,6 +242,9 @@ def main():
             from paper_2311_00869_gb300 import autotune
 
             tuned = autotune.tune(sb, K=TREES, R=args.R)
+        elif args.gl_lanes:
+            sb.set_tuning(gl_lanes=args.gl_lanes)
+            tuned = {"gl_lanes": args.gl_lanes}
         res = graphl_leg(P, sb, n1, m1, R=args.R, steps=args.gl_steps)
         res["tuning"] = tuned
         line = {"leg": "graphl", "metric": "graphL steps/s", "value": res["graphl_steps_per_s"], "unit": "steps/s",
