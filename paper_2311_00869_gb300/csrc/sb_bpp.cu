@@ -161,29 +161,39 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
             const unsigned cmax = __reduce_max_sync(gmask, (unsigned)cnt);
             if (cmax * G <= 2 * Tsum + 2 * G) {
                 // the lanes' shares are even enough: every lane hashes its own
-                // candidates into its own slots, two at a time, no queue
+                // candidates into its own slots (32-bit halves, two at a time),
+                // with no queue and no synchronisation
+                const uint32_t* ak = akey + KSLOT(gl, 0);
+                uint32_t* bs = best + BSLOT(tid, 0);
+                uint8_t* lb = labb + LSLOT(tid, 0);
 #pragma unroll
                 for (int k = 0; k < 8; k++) {
                     const uint32_t u = (c[k] & SB_ID_MASK) - goff;
                     const uint32_t hx = u ^ y;
-                    for (uint64_t b = f[k]; b;) {
-                        const int ta = __ffsll((long long)b) - 1;
-                        b &= b - 1;
-                        const int tb = b ? __ffsll((long long)b) - 1 : ta;
-                        const bool two = b != 0;
-                        b &= b - 1;
-                        const uint32_t ha = sb_fmix32(hx + akey[KSLOT(gl, ta)]);
-                        const uint32_t hb = sb_fmix32(hx + akey[KSLOT(gl, tb)]);
-                        const uint32_t ba = best[BSLOT(tid, ta)], bb = best[BSLOT(tid, tb)];
-                        if (ha <= ba) {  // <=: the minima start at 0xFFFFFFFF
-                            best[BSLOT(tid, ta)] = ha;
-                            labb[LSLOT(tid, ta)] = (uint8_t)((l[k] >> ta) & 1ull);
-                            if (PAR) bestu[BSLOT(tid, ta)] = (int32_t)u;
-                        }
-                        if (two && hb <= bb) {
-                            best[BSLOT(tid, tb)] = hb;
-                            labb[LSLOT(tid, tb)] = (uint8_t)((l[k] >> tb) & 1ull);
-                            if (PAR) bestu[BSLOT(tid, tb)] = (int32_t)u;
+#pragma unroll
+                    for (int half = 0; half < 2; half++) {
+                        uint32_t m = (uint32_t)(f[k] >> (32 * half));
+                        const uint32_t lw = (uint32_t)(l[k] >> (32 * half));
+                        const int t0 = 32 * half;
+                        while (m) {
+                            const int ia = __ffs(m) - 1;
+                            m &= m - 1;
+                            const int ib = m ? __ffs(m) - 1 : ia;
+                            const bool two = m != 0;
+                            m &= m - 1;
+                            const uint32_t ha = sb_fmix32(hx + ak[t0 + ia]);
+                            const uint32_t hb = sb_fmix32(hx + ak[t0 + ib]);
+                            const uint32_t ba = bs[t0 + ia], bb = bs[t0 + ib];
+                            if (ha <= ba) {  // <=: the minima start at 0xFFFFFFFF
+                                bs[t0 + ia] = ha;
+                                lb[t0 + ia] = (uint8_t)((lw >> ia) & 1u);
+                                if (PAR) bestu[BSLOT(tid, t0 + ia)] = (int32_t)u;
+                            }
+                            if (two && hb <= bb) {
+                                bs[t0 + ib] = hb;
+                                lb[t0 + ib] = (uint8_t)((lw >> ib) & 1u);
+                                if (PAR) bestu[BSLOT(tid, t0 + ib)] = (int32_t)u;
+                            }
                         }
                     }
                 }
