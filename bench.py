@@ -542,6 +542,11 @@ def batch_leg(args, P):
     nv, mv = sb.load_batch(graphs)
     K, R = 256, 32
     n_tot, m_tot = int(nv.sum()), int(mv.sum())
+    tuned = {"default": True}
+    if not args.no_tune:
+        from paper_2311_00869_gb300 import autotune
+
+        tuned = autotune.tune(sb, K=K, R=R)
     for i in range(args.warmup):
         sb.sample_trees(SEED, i * K, K)
         sb.batch_cloud(want_entries=False)
@@ -579,6 +584,7 @@ def batch_leg(args, P):
         "fr_min_median": float(np.median(cl["fr_min"])),
         "states_median": float(np.median(cl["n_states"])),
         "graphl_F_median": float(np.median(F_final.cpu().numpy())),
+        "tuning": tuned,
     }
     print(json.dumps(line), flush=True)
     sb.close()

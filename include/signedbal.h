@@ -258,8 +258,10 @@ sb_status sb_graphL_fwd(sb_ctx* ctx, const float* gamma, int32_t R, float* loss_
 
 /*
  * Adjoint of sb_graphL_fwd (Eq. 4): grad_out[v*R + r] =
- * -1/2 * gout[r] * sum_{j in N(v)} e_vj gamma[j*R + r], summed over CSR rows
- * in a fixed order (no float atomics; bitwise reproducible).  Device pointers.
+ * -1/2 * gout[g*R + r] * sum_{j in N(v)} e_vj gamma[j*R + r], g = the graph
+ * of v (0 for one graph; gout is G x R in a batch, like the losses),
+ * summed over CSR rows in a fixed order (no float atomics; bitwise
+ * reproducible).  Device pointers.
  */
 sb_status sb_graphL_bwd(sb_ctx* ctx, const float* gamma, int32_t R, const float* gout, float* grad_out);
 

@@ -112,7 +112,7 @@ def tune(sb, K: int = 1024, R: int | None = None, seed: int = 987654321, reps: i
     if R:
         gen = torch.Generator(device="cpu").manual_seed(1)
         g0 = (torch.rand((sb.n, R), generator=gen) * 2 - 1).to(sb.device)
-        grad_out = torch.ones(R, device=sb.device)
+        grad_out = torch.ones(sb._per_graph() * R, device=sb.device)  # G x R in a batch
         best = None
         for lanes in ((8, 32) if R % 4 == 0 else (8,)):
             sb.set_tuning(gl_lanes=lanes)

@@ -597,9 +597,40 @@ __global__ void __launch_bounds__(256) k_state_hash(const uint64_t* __restrict__
     const int b = threadIdx.x & 63, sub = threadIdx.x >> 6;
     const int64_t v0 = (int64_t)blockIdx.x * HASH_VCHUNK;
     const int64_t v1 = min(n, v0 + HASH_VCHUNK);
-    int64_t gcur = -1;
-    uint64_t fl = 0, acc = 0;
-    for (int64_t v = v0 + sub; v < v1; v += 4) {
+    int64_t gcur = vgid ? vgid[min(v0 + sub, n - 1)] : 0;
+    uint64_t fl = flipw[gcur * W + w], acc = 0;
+    int64_t v = v0 + sub;
+    // 8 vertices (stride 4) per round: their label words and weights are
+    // loaded before any is added
+    for (; v + 28 < v1; v += 32) {
+        uint64_t x[8], wt[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            x[i] = lab[(v + 4 * i) * W + w];
+            wt[i] = weight[v + 4 * i];
+        }
+        bool same = true;
+        if (vgid) {
+#pragma unroll
+            for (int i = 0; i < 8; i++) same = same && vgid[v + 4 * i] == gcur;
+        }
+        if (same) {
+#pragma unroll
+            for (int i = 0; i < 8; i++) acc += (((x[i] ^ fl) >> b) & 1ull) ? wt[i] : 0ull;
+        } else {
+            for (int i = 0; i < 8; i++) {
+                const int64_t g = vgid[v + 4 * i];
+                if (g != gcur) {
+                    if (acc) atomicAdd(H + gcur * KP + 64 * w + b, (unsigned long long)acc);
+                    acc = 0;
+                    gcur = g;
+                    fl = flipw[g * W + w];
+                }
+                acc += (((x[i] ^ fl) >> b) & 1ull) ? wt[i] : 0ull;
+            }
+        }
+    }
+    for (; v < v1; v += 4) {
         const int64_t g = vgid ? vgid[v] : 0;
         if (g != gcur) {
             if (acc) atomicAdd(H + gcur * KP + 64 * w + b, (unsigned long long)acc);
@@ -607,9 +638,7 @@ __global__ void __launch_bounds__(256) k_state_hash(const uint64_t* __restrict__
             gcur = g;
             fl = flipw[g * W + w];
         }
-        const uint64_t x = lab[v * W + w] ^ fl;
-        const uint64_t wt = weight[v];
-        acc += ((x >> b) & 1ull) ? wt : 0ull;
+        acc += (((lab[v * W + w] ^ fl) >> b) & 1ull) ? weight[v] : 0ull;
     }
     if (acc) atomicAdd(H + gcur * KP + 64 * w + b, (unsigned long long)acc);
 }

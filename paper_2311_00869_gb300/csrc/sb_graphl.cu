@@ -24,7 +24,7 @@ struct GlArgs {
     const float* gin;      // n x R input
     float* gout_rows;      // n x R output
     float* partial;        // partial sums of split rows
-    const float* upstream; // GRAD: gout[R]
+    const float* upstream; // GRAD: gout[G x R] (G = 1 for one graph)
     const float* scale;    // STEP: input scale per (graph, column), a power of two
     float half_alpha;      // STEP: alpha / 2
     int32_t* F;            // STEP: discrete-loss accumulator (x2) per (graph, column), nullable
@@ -89,7 +89,7 @@ __device__ __forceinline__ uint32_t gl_emit(const GlArgs& A, int64_t v, int64_t 
 {
     const int64_t idx = v * A.R + r;
     if (!STEP) {
-        A.gout_rows[idx] = -0.5f * A.upstream[r] * acc;
+        A.gout_rows[idx] = -0.5f * A.upstream[g * A.R + r] * acc;  // gout is G x R in a batch
         return 0u;
     }
     const float sc = A.scale[g * A.R + r];

@@ -79,6 +79,9 @@ def test_batch_graphl_per_graph():
     loss, F = sb.graphL_fwd(G0)  # G x R in a batch
     loss = loss.reshape(len(graphs), R).cpu().numpy()
     F = F.reshape(len(graphs), R).cpu().numpy()
+    # adjoint with a different upstream weight for every (graph, column)
+    gout = np.random.default_rng(5).uniform(0.5, 2.0, size=(len(graphs), R)).astype(np.float32)
+    grad = sb.graphL_bwd(G0, torch.from_numpy(gout.reshape(-1)).cuda()).cpu().numpy()
     out, exps, F_trace, F_final = sb.graphL_descent(G0, 0.05, 60, renorm_log2=16, trace=True)
     exps = exps.reshape(len(graphs), R).cpu().numpy()
     F_final = F_final.reshape(len(graphs), R).cpu().numpy()
@@ -89,6 +92,8 @@ def test_batch_graphl_per_graph():
         prod = np.abs(gam[sl][r.eu].astype(np.float64) * gam[sl][r.ev])
         assert np.array_equal(F[g], F64), g
         assert np.all(np.abs(loss[g] - L64) <= 1e-5 * (0.5 * (1.0 + prod)).sum(axis=0) + 1e-6), g
+        g64 = O.graphl_grad_f64(r, gam[sl].astype(np.float64), gout[g].astype(np.float64))
+        assert np.linalg.norm(grad[sl] - g64) <= 1e-5 * np.linalg.norm(g64) + 1e-6, g
         ref, rexps, _ = O.graphl_descent_f64(r, gam[sl], 0.05, 60, renorm_log2=16)
         got = out[sl].astype(np.float64) * np.exp2(exps[g].astype(np.float64))[None, :]
         want = ref * np.exp2(rexps.astype(np.float64))[None, :]
