@@ -181,8 +181,13 @@ class SignedBal:
         return out
 
     def frustration(self, counts=None, hashes=None):
-        counts = torch.empty(self.K, dtype=torch.int32, device=self.device) if counts is None else counts
-        hashes = torch.empty(self.K, dtype=torch.int64, device=self.device) if hashes is None else hashes
+        """Counts and hashes of the last sample: K each, or G x K in a batch."""
+        shape = (self.batch_G, self.K) if getattr(self, "batch_G", 0) else (self.K,)
+        need = int(np.prod(shape))
+        counts = torch.empty(shape, dtype=torch.int32, device=self.device) if counts is None else counts
+        hashes = torch.empty(shape, dtype=torch.int64, device=self.device) if hashes is None else hashes
+        if counts.numel() < need or hashes.numel() < need:
+            raise ValueError(f"counts / hashes need {need} entries")
         self._check(self.lib.sb_frustration(self.h, _ptr(counts), _ptr(hashes)))
         return counts, hashes
 
