@@ -13,7 +13,7 @@
 
 #define SB_WORDS_MAX 32          // 64-tree words processed per BFS launch
 #define SB_TREES_MAX (64 * 64)   // trees per sb_sample_trees call
-#define SB_BFS_CHUNK 256         // CSR entries per BFS work item
+#define SB_BFS_CHUNK 512         // CSR entries per BFS work item
 #define SB_GL_CHUNK 256          // CSR entries per graphL work item
 #define SB_NEG_BIT 0x80000000u   // sign bit packed into CSR / edge-list ids
 #define SB_ID_MASK 0x7FFFFFFFu

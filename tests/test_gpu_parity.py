@@ -127,10 +127,10 @@ def test_trees_labels_counts_small(P, sb, K):
 
 
 def test_split_rows_hub(P, sb):
-    # vertex 0 joins 700 others (split into several chunks) plus a random mesh
-    n, a, b, s = _hub_graph(seed=77, n=701, extra=900, neg=0.35)
+    # vertex 0 joins 2000 others (split into several chunks) plus a random mesh
+    n, a, b, s = _hub_graph(seed=77, n=2001, extra=2600, neg=0.35)
     g = load_both(sb, n, a, b, s)
-    assert np.diff(g.rowptr).max() > 512
+    assert np.diff(g.rowptr).max() > 1536
     check_batch(P, sb, g, seed=5, t0=0, K=200, parents=True)
     check_batch(P, sb, g, seed=6, t0=0, K=2048 + 33, parents=False)
 
