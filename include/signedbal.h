@@ -121,9 +121,9 @@ sb_status sb_get_tuning(sb_ctx* ctx, int32_t knob, int64_t* value);
 /* Work counters of the last sb_sample_trees call (host array, n entries,
    n <= SB_STATS_N): [0] BFS levels (largest over its launches), [1] BFS
    launches, [2] neighbour entries scanned (per vertex-word lane),
-   [3] hashed parent candidates of whole rows, [4] second-pass entries
-   (trees with two or more candidates), [5] hashed parent candidates of split
-   rows.  Synchronises the stream. */
+   [3] hashed parent candidates of whole rows, [4] always 0 (kept so that
+   the layout stays; every row is scanned in one pass), [5] hashed parent
+   candidates of split rows.  Synchronises the stream. */
 #define SB_STATS_N 6
 sb_status sb_stats(sb_ctx* ctx, int64_t* out, int32_t n);
 

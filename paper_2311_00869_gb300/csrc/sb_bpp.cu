@@ -105,29 +105,24 @@ __device__ __forceinline__ int group_excl_scan(int x, unsigned gmask, int gl, in
 
 // One pass over a CSR range for one vertex: lane gl of the group owns word
 // w0 + gl.  Neighbours are read 8 at a time so that 8 frontier gathers are in
-// flight per lane.
-//   HASH = false: once / twice = trees reached through >= 1 / >= 2 candidates,
-//                 labx = candidate label bits (exact where once & ~twice).
-//   HASH = true : running argmin of the hashed parent key over the candidates
-//                 in `mask`.  The group's candidate bits are compacted into a
-//                 shared queue (entry = neighbour, owner lane, tree, label
-//                 bit) and hashed by all lanes of the group in lockstep: the
-//                 8 neighbours of a tile at once (atomicMin, then the entry
-//                 equal to the minimum writes its label), or, when they hold
-//                 more candidates than the queue, one neighbour at a time (its
-//                 entries have distinct slots).  best (initialised to
-//                 0xFFFFFFFF) holds the smallest hash, labb / bestu the
-//                 winner's label bit / id; keys are distinct (the hash is a
-//                 bijection in u), so `h <= best` accepts exactly the minimum.
-//                 `once` returns the trees seen.
+// flight per lane.  It keeps the running argmin of the hashed parent key over
+// the candidates in `mask`: best (initialised to 0xFFFFFFFF) holds the
+// smallest hash, labb / bestu the winner's label bit / id; keys are distinct
+// (the hash is a bijection in u), so `h <= best` accepts exactly the minimum.
+// `once` returns the trees that had a candidate.  For each tile of 8
+// neighbours the lanes hash their own candidates when their shares are even;
+// otherwise the group's candidate bits are compacted into a shared queue
+// (entry = neighbour, owner lane, tree, label bit) and hashed by all lanes in
+// lockstep: the 8 neighbours at once (atomicMin, then the entry equal to the
+// minimum writes its label), or, when they hold more candidates than the
+// queue, one neighbour at a time (its entries have distinct slots).
 // `cur` and `lab` are rewritten between levels by other blocks, so they are
 // read with plain (coherent) loads; the column array is read-only.
-template <bool HASH, bool PAR, int BD, int G>
+template <bool PAR, int BD, int G>
 __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint64_t* cur, const uint64_t* lab, int Wb,
                                          int Wt, int wofs, int gl, uint64_t mask, uint32_t y, uint32_t goff,
                                          const uint32_t* akey, uint32_t* best, uint8_t* labb, int32_t* bestu,
-                                         uint16_t* queue, int tid, unsigned gmask, uint64_t& once, uint64_t& twice,
-                                         uint64_t& labx, uint32_t& nhash)
+                                         uint16_t* queue, int tid, unsigned gmask, uint64_t& once, uint32_t& nhash)
 {
     for (int j = 0; j < len; j += 8) {
         uint32_t c[8];
@@ -140,14 +135,7 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
 #pragma unroll
         for (int k = 0; k < 8; k++)
             l[k] = f[k] ? (lab[(int64_t)(c[k] & SB_ID_MASK) * Wt + wofs] ^ ((c[k] >> 31) ? ~0ull : 0ull)) : 0ull;
-        if (!HASH) {
-#pragma unroll
-            for (int k = 0; k < 8; k++) {
-                twice |= once & f[k];
-                once |= f[k];
-                labx |= f[k] & l[k];
-            }
-        } else {
+        {
             const int owner0 = tid - gl;  // thread index of the group's lane 0
             int cnt = 0;
 #pragma unroll
@@ -356,7 +344,7 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
     const int Wb = A.Wb, Wt = A.Wt, w0 = A.w0;
     const int wofs = w0 + gl;
     uint16_t* queue = queues + (tid / G) * (BFS_QUEUE_PER_LANE * G);
-    uint32_t n_scan = 0, n_hash = 0, n_pass2 = 0, n_hash_hub = 0;  // work counters
+    uint32_t n_scan = 0, n_hash = 0, n_hash_hub = 0;  // work counters
     int L = 1;
     while (true) {
         const uint64_t* cur = (L & 1) ? A.fr0 : A.fr1;
@@ -381,32 +369,20 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
                 const int32_t* cp = A.col + itm.beg;
                 const int len = itm.end - itm.beg;
                 const bool hub = itm.hub >= 0;
-                uint64_t once = 0, twice = 0, labx = 0;
-                // the passes below synchronise the group's lanes, so every lane of
-                // the group enters them (a lane with nothing to do has mask 0)
+                uint64_t once = 0, labx = 0;
+                // the pass below synchronises the group's lanes, so every lane of
+                // the group enters it (a lane with nothing to do has mask 0)
                 if (__any_sync(gmask, U != 0)) {
                     const uint32_t goff = A.vgoff ? (uint32_t)A.vgoff[v] : 0u;
                     const uint32_t y = sb_child_salt(A.S, (uint32_t)v - goff);
                     if (U) n_scan += (uint32_t)len;
-                    if (!hub && !PAR) {
-                        scan_row<false, PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, goff, akey, best, labb,
-                                                    bestu, queue, tid, gmask, once, twice, labx, n_hash);
-                        if (__any_sync(gmask, twice != 0)) {
-                            // trees reached through two or more candidates: hashed argmin
-                            uint64_t o2 = 0, t2 = 0, l2 = 0;
-                            if (twice) n_pass2 += (uint32_t)len;
-                            best_reset<BD>(best, tid, twice);
-                            scan_row<true, PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, twice, y, goff, akey, best,
-                                                       labb, bestu, queue, tid, gmask, o2, t2, l2, n_hash);
-                            labx = (labx & ~twice) | (winner_labels<BD>(labb, tid, twice) & twice);
-                        }
-                    } else {
-                        best_reset<BD>(best, tid, U);
-                        scan_row<true, PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, goff, akey, best, labb,
-                                                   bestu, queue, tid, gmask, once, twice, labx,
-                                                   hub ? n_hash_hub : n_hash);
-                        labx = winner_labels<BD>(labb, tid, once);
-                    }
+                    // one pass: every candidate of every open tree is hashed (a
+                    // first pass that singled out the trees with two or more
+                    // candidates cost more than the few hashes it saved)
+                    best_reset<BD>(best, tid, U);
+                    scan_row<PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, goff, akey, best, labb, bestu,
+                                         queue, tid, gmask, once, hub ? n_hash_hub : n_hash);
+                    labx = winner_labels<BD>(labb, tid, once);
                 }
                 if (hub) {
                     // chunk of a split row: publish the chunk minima, one atomic per tree
@@ -513,13 +489,11 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
     for (int d = 16; d; d >>= 1) {
         n_scan += __shfl_xor_sync(0xffffffffu, n_scan, d);
         n_hash += __shfl_xor_sync(0xffffffffu, n_hash, d);
-        n_pass2 += __shfl_xor_sync(0xffffffffu, n_pass2, d);
         n_hash_hub += __shfl_xor_sync(0xffffffffu, n_hash_hub, d);
     }
     if ((tid & 31) == 0) {
         atomicAdd((unsigned long long*)(A.sync + 8), (unsigned long long)n_scan);
         atomicAdd((unsigned long long*)(A.sync + 10), (unsigned long long)n_hash);
-        atomicAdd((unsigned long long*)(A.sync + 12), (unsigned long long)n_pass2);
         atomicAdd((unsigned long long*)(A.sync + 14), (unsigned long long)n_hash_hub);
     }
 }
