@@ -13,6 +13,7 @@
 #include "sb_internal.cuh"
 
 #define GL_THREADS 256
+#define GL_ROWS_MIN_BLOCKS 1  // blocks per SM the row kernel's registers must allow
 
 struct GlArgs {
     const sb_bfs_item* items;   // chunks of split rows first, then whole rows
@@ -108,7 +109,7 @@ __device__ __forceinline__ uint32_t gl_emit(const GlArgs& A, int64_t v, int64_t 
 // block (rows in vertex order) rarely crosses a graph of a batch.
 #define GL_ITEM_BLOCK 16
 template <int VEC, int SL, bool STEP>
-__global__ void __launch_bounds__(GL_THREADS) k_gl_rows(GlArgs A)
+__global__ void __launch_bounds__(GL_THREADS, GL_ROWS_MIN_BLOCKS) k_gl_rows(GlArgs A)
 {
     extern __shared__ uint32_t gsm[];
     int32_t* sF = (int32_t*)gsm;  // R
