@@ -371,7 +371,7 @@ def _src_digest(paths):
 # kernel sources still match the digest taken when it was captured.
 _BPP_SRC = ("paper_2311_00869_gb300/csrc/sb_bpp.cu", "paper_2311_00869_gb300/csrc/sb_internal.cuh")
 NCU_TRAFFIC = {
-    "bfs": (4166870784 + 1842486528, _BPP_SRC, "3dc09817e122dcc2d87ffa71cfe10bf48fe66c727621dfcdfa12ee9965dca77d"),
+    "bfs": (3528443136 + 1342137344, _BPP_SRC, "d4bcbdcb9aac2d6c320c1c18e50e13c4176e6885244c8a1629d0931522488fb7"),
 }
 
 

@@ -13,7 +13,7 @@
 #include "sb_internal.cuh"
 
 #define GL_THREADS 256
-#define GL_ROWS_MIN_BLOCKS 1  // blocks per SM the row kernel's registers must allow
+#define GL_ROWS_MIN_BLOCKS 4  // blocks per SM the row kernel's registers must allow
 
 struct GlArgs {
     const sb_bfs_item* items;   // chunks of split rows first, then whole rows
@@ -646,7 +646,8 @@ extern "C" sb_status sb_graphL_descent(sb_ctx* c, const float* gamma0, float* ga
                               (uint64_t)(uintptr_t)F_trace, (uint64_t)(uintptr_t)c->gl_buf,
                               (uint64_t)(uintptr_t)c->gl_scale, (uint64_t)(uintptr_t)c->gl_partial,
                               (uint64_t)(uintptr_t)c->gl_misc, (uint64_t)(uintptr_t)c->gl_colmax,
-                              (uint64_t)(uintptr_t)c->gl_items, (uint64_t)c->n, 1};
+                              (uint64_t)(uintptr_t)c->gl_items, (uint64_t)c->n,
+                              1 + (uint64_t)c->tune[SB_TUNE_GL_LANES]};  // the captured kernels depend on it
     const float* last = src;
     for (int s = 0; s < steps; s++) last = (last == gamma_out) ? c->gl_buf : gamma_out;
     if (steps > 0) {
