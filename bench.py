@@ -162,14 +162,20 @@ def oracle_trees(g, t0, count, cores):
     return time.perf_counter() - t
 
 
-def cpu_baseline(g, budget_s=12.0):
+def cpu_baseline(g, budget_s=12.0, single_budget_s=3.0):
     cores = os.cpu_count() or 1
     done, el = 0, 0.0
     while el < budget_s:
         el += oracle_trees(g, 10_000_000 + done, cores, cores)
         done += cores
+    one, el1 = 0, 0.0
+    while el1 < single_budget_s:
+        el1 += oracle_trees(g, 20_000_000 + one, 1, 1)
+        one += 1
     return {"value": done * g.m / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{done} trees (BFS tree, labels, count, hash) of the same graph, {cores} threads, {el:.1f} s"}
+            "sample": f"{done} trees (BFS tree, labels, count, hash) of the same graph, {cores} threads, {el:.1f} s",
+            "single_thread": {"value": one * g.m / el1, "unit": UNIT, "cores": 1,
+                              "sample": f"{one} trees on one thread, {el1:.1f} s"}}
 
 
 def run_reference(args):
@@ -245,7 +251,7 @@ def main():
         elif args.gl_lanes:
             sb.set_tuning(gl_lanes=args.gl_lanes)
             tuned = {"gl_lanes": args.gl_lanes}
-        res = graphl_leg(P, sb, n1, m1, R=args.R, steps=args.gl_steps)
+        res = graphl_leg(P, sb, n1, m1, R=args.R, steps=args.gl_steps, plain_inits=4)
         res["tuning"] = tuned
         line = {"leg": "graphl", "metric": "graphL steps/s", "value": res["graphl_steps_per_s"], "unit": "steps/s",
                 "n_gpus": 1, "steps": args.gl_steps, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
@@ -305,7 +311,7 @@ def main():
 
     cl, fr_min = sb.cloud()
     extras = {"fr_min": int(fr_min), "distinct_states": int(cl["S"].shape[0]), "tuning": tuned,
-              "bfs_stats": sb.stats()}
+              "bfs_stats": sb.stats(), "trees_per_s": world * TREES / (ms_step / 1000.0)}
     if dist:  # host-side merge of the rank clouds, after the timed region
         from paper_2311_00869_gb300 import shard
 
@@ -475,7 +481,7 @@ def plain_leg(sb, m):
             "plain_vs_batched_same_cloud": same, "plain64_fr_min": int(c_plain["S"].min())}
 
 
-def graphl_leg(P, sb, n, m, R=256, steps=50, alpha=0.05):
+def graphl_leg(P, sb, n, m, R=256, steps=50, alpha=0.05, plain_inits=0):
     import torch
 
     import synth
@@ -495,9 +501,32 @@ def graphl_leg(P, sb, n, m, R=256, steps=50, alpha=0.05):
     prof = sb.profile_read()
     ms = e0.elapsed_time(e1)
     F0, _ = sb.graphL_round(g0)
-    return {"graphl_steps_per_s": steps / (ms / 1000.0), "graphl_R": R, "graphl_steps": steps,
-            "graphl_init_steps_per_s": R * steps / (ms / 1000.0), "graphl_F_min_start": int(F0.min()),
-            "graphl_F_min_final": int(F_final.min()), "graphl_row_kernel_ms_per_step": prof["gl_rows"][0] / steps}
+    res = {"graphl_steps_per_s": steps / (ms / 1000.0), "graphl_R": R, "graphl_steps": steps,
+           "graphl_init_steps_per_s": R * steps / (ms / 1000.0), "graphl_F_min_start": int(F0.min()),
+           "graphl_F_min_final": int(F_final.min()), "graphl_row_kernel_ms_per_step": prof["gl_rows"][0] / steps}
+    if plain_inits:
+        # untimed: the discrete loss before every 50th step
+        _, _, F_trace, _ = sb.graphL_descent(g0, alpha, steps, trace=True, out=out)
+        res["graphl_F_min_every_50"] = [int(x) for x in F_trace[::50].min(dim=1).values.cpu()]
+        # plain: one start point per launch, the same columns, must reach the same F
+        Fb = F_final.cpu()
+        same = True
+        t_plain = 0.0
+        for r in range(plain_inits):
+            col = g0[:, r:r + 1].contiguous()
+            o1 = torch.empty_like(col)
+            sb.graphL_descent(col, alpha, steps, out=o1)
+            torch.cuda.synchronize()
+            e0.record()
+            _, _, _, F1 = sb.graphL_descent(col, alpha, steps, out=o1)
+            e1.record()
+            torch.cuda.synchronize()
+            t_plain += e0.elapsed_time(e1)
+            same = same and int(F1[0]) == int(Fb[r])
+        res["graphl_plain_init_steps_per_s"] = plain_inits * steps / (t_plain / 1000.0)
+        res["graphl_plain_inits"] = plain_inits
+        res["graphl_plain_same_F"] = same
+    return res
 
 
 def e2e_leg(P, sb, n, u, v, s, steps=3):
@@ -526,6 +555,23 @@ def e2e_leg(P, sb, n, u, v, s, steps=3):
     return {"value": steps * TREES * m1 / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "includes": "H2D of the COO, ingest, sample, count, cloud, D2H"}
 
+
+
+def batch_cpu_baseline(graphs, K, count=64):
+    """The oracle on `count` graphs of the batch drawn with a fixed seed, K
+    trees each, on all host cores; edge-evals/s over that subset."""
+    import oracle as O
+
+    cores = os.cpu_count() or 1
+    idx = np.random.default_rng(7).choice(len(graphs), size=min(count, len(graphs)), replace=False)
+    gs = [O.clean_graph(*graphs[i]) for i in idx]
+    t = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(lambda g: O.sample(g, SEED, 0, K, want_labels=False), gs))
+    el = time.perf_counter() - t
+    m_sub = sum(g.m for g in gs)
+    return {"value": K * m_sub / el, "unit": "edge-evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(gs)} of the graphs (seeded choice, {m_sub} edges), {K} trees each, {el:.1f} s"}
 
 
 def batch_leg(args, P):
@@ -586,6 +632,10 @@ def batch_leg(args, P):
         "graphl_F_median": float(np.median(F_final.cpu().numpy())),
         "tuning": tuned,
     }
+    try:
+        line["cpu_baseline"] = batch_cpu_baseline(graphs, K)
+    except Exception as e:  # the baseline must not hide the main number
+        line["cpu_baseline"] = {"error": repr(e)}
     print(json.dumps(line), flush=True)
     sb.close()
     return 0

@@ -312,14 +312,21 @@ def test_graphl_descent_and_round(P, sb):
 
 # ------------------------------------------------- full size, sampled trees
 
-def test_rmat_2pow20_sampled_trees(P, sb):
+@pytest.fixture(scope="module")
+def rmat20():
+    """The 2^20-vertex, 2^24-edge two-faction R-MAT graph of the benchmark,
+    raw and as the oracle cleans it."""
+    n, u, v, s = synth.rmat_two_faction(scale=20, m_target=1 << 24)
+    return (n, u, v, s), O.clean_graph(n, u, v, s)
+
+
+def test_rmat_2pow20_sampled_trees(P, sb, rmat20):
     """The 2^20-vertex, 2^24-edge two-faction R-MAT graph in the benchmark's
     launch configuration (K = 1024 trees in one batch): trees 0 and 1023 are
     checked against the oracle bit for bit; every count is checked against
     the bound given by its own labels."""
-    n, u, v, s = synth.rmat_two_faction(scale=20, m_target=1 << 24)
+    (n, u, v, s), g = rmat20
     n1, m1, _ = sb.load_graph(n, u, v, s)
-    g = O.clean_graph(n, u, v, s)
     assert (n1, m1) == (g.n, g.m)
     K = 1024
     sb.sample_trees(0, 0, K)
@@ -333,3 +340,47 @@ def test_rmat_2pow20_sampled_trees(P, sb):
         lab = ((labw[:, t // 64] >> np.uint64(t % 64)) & np.uint64(1)).astype(np.uint8)
         assert np.array_equal(lab, ref["labels"][0])
     assert np.all(counts >= 0) and np.all(counts <= g.m - g.n + 1)
+
+
+def test_graphl_gradient_central_differences_2000_vertex_subgraph(P, sb, rmat20):
+    """The adjoint on a 2,000-vertex piece of the benchmark graph (the first
+    2,000 vertices a BFS from vertex 0 reaches, their induced subgraph, its
+    largest component) against float64 central differences of the oracle's
+    relaxed loss (Eq. 3).  The loss is linear in every single coordinate, so
+    the central difference is exact up to rounding; the float32 gradient
+    must agree within 1e-5 relative (Eq. 4)."""
+    import collections
+
+    _, g = rmat20
+    seen = np.full(g.n, -1, np.int64)
+    seen[0] = 0
+    order, dq = [0], collections.deque([0])
+    while dq and len(order) < 2000:
+        x = dq.popleft()
+        for y in g.col[g.rowptr[x]:g.rowptr[x + 1]]:
+            if seen[y] < 0 and len(order) < 2000:
+                seen[y] = len(order)
+                order.append(int(y))
+                dq.append(int(y))
+    keep = (seen[g.eu] >= 0) & (seen[g.ev] >= 0)
+    su, sv = seen[g.eu[keep]].astype(np.int32), seen[g.ev[keep]].astype(np.int32)
+    ss = np.where(g.eneg[keep] != 0, -1, 1).astype(np.int8)
+    gs = load_both(sb, len(order), su, sv, ss)
+    R = 8
+    gam = synth.gamma0(gs.n, R, seed=3)
+    gout = np.random.default_rng(9).uniform(0.5, 2.0, R).astype(np.float32)
+    grad = sb.graphL_bwd(torch.from_numpy(gam).cuda(), torch.from_numpy(gout).cuda()).cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(13)
+    vs, rs = rng.integers(0, gs.n, 64), rng.integers(0, R, 64)
+    g64 = gam.astype(np.float64)
+    fd = np.zeros(64)
+    for i, (vv, rr) in enumerate(zip(vs, rs)):
+        h = 1e-4 * max(1.0, abs(g64[vv, rr]))
+        gp, gm = g64.copy(), g64.copy()
+        gp[vv, rr] += h
+        gm[vv, rr] -= h
+        Lp, _ = O.graphl_loss_f64(gs, gp)
+        Lm, _ = O.graphl_loss_f64(gs, gm)
+        fd[i] = gout[rr] * (Lp[rr] - Lm[rr]) / (2 * h)
+    got = grad[vs, rs]
+    assert np.linalg.norm(got - fd) <= 1e-5 * np.linalg.norm(fd) + 1e-7
