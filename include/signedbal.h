@@ -245,6 +245,15 @@ sb_status sb_cloud_reset(sb_ctx* ctx, int64_t max_states, int32_t hash_bits);
    host or device. */
 sb_status sb_cloud_state(sb_ctx* ctx, int64_t idx, uint64_t* bits_out);
 
+/* The edges that cloud state `idx` (order of sb_cloud) switches to reach its
+   balanced signing -- the paper's output "list of edges to switch" (Sec. 3,
+   the frustration cloud; Sec. 6): bit e % 64 of edge_bits_out[e / 64] is 1
+   when edge e (order of sb_graph_edges) has lab[u] ^ lab[v] ^ neg = 1.
+   ceil(m/64) words, host or device; n_switched_out (host, nullable)
+   receives their number, which equals the state's S.  Not available on a
+   batch of graphs (SB_ERR_STATE); synchronises the stream. */
+sb_status sb_cloud_switch(sb_ctx* ctx, int64_t idx, uint64_t* edge_bits_out, int64_t* n_switched_out);
+
 /* ------------------------------------------------------------------ graphL */
 
 /*

@@ -218,6 +218,14 @@ class SignedBal:
     def cloud_reset(self, max_states=0, hash_bits=0):
         self._check(self.lib.sb_cloud_reset(self.h, max_states, hash_bits))
 
+    def cloud_switch(self, idx):
+        """(bits, count): int64 words with bit e set for every edge (order of
+        graph_edges) that cloud state `idx` switches, and their number (= S)."""
+        out = torch.empty((self.m + 63) // 64, dtype=torch.int64, device=self.device)
+        cnt = ctypes.c_int64()
+        self._check(self.lib.sb_cloud_switch(self.h, idx, _ptr(out), ctypes.byref(cnt)))
+        return out, cnt.value
+
     def cloud_state(self, idx):
         out = torch.empty((self.n + 63) // 64, dtype=torch.int64, device=self.device)
         self._check(self.lib.sb_cloud_state(self.h, idx, _ptr(out)))

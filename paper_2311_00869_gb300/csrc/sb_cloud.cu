@@ -356,9 +356,16 @@ extern "C" sb_status sb_cloud(sb_ctx* c, sb_cloud_entry* out, int64_t cap, int64
     return SB_OK;
 }
 
-extern "C" sb_status sb_cloud_state(sb_ctx* c, int64_t idx, uint64_t* bits_out)
+static sb_status cuda_st(sb_ctx* c, cudaError_t e, const char* what)
 {
-    if (!c || !bits_out) return SB_ERR_ARG;
+    return e == cudaSuccess ? SB_OK : sb_cuda_fail(c, e, what);
+}
+
+// Device copy of the canonical labels of cloud state `idx` (order of
+// sb_cloud) in a buffer from sb_dalloc that the caller frees.
+static sb_status cloud_state_dev(sb_ctx* c, int64_t idx, uint64_t** out)
+{
+    *out = nullptr;
     if (!c->has_graph || !c->cl_table) return sb_fail(c, SB_ERR_STATE, "no cloud");
     SB_CHECK_CUDA(c, cudaSetDevice(c->device));
     if (c->has_batch && !c->batch_in_cloud) SB_TRY(sb_cloud_insert_batch(c));
@@ -381,9 +388,78 @@ extern "C" sb_status sb_cloud_state(sb_ctx* c, int64_t idx, uint64_t* bits_out)
     k_cloud_gather<<<(unsigned)std::min<int64_t>(sb_cdiv(nchunks, 256), 4096), 256, 0, c->stream>>>(
         c->cl_bits, nchunks, c->cl_max, idx, tmp);
     sb_status st = sb_after_launch(c, "k_cloud_gather");
-    if (st == SB_OK) st = sb_copy_out(c, bits_out, tmp, sizeof(uint64_t) * (size_t)nchunks);
+    if (st != SB_OK) {
+        cudaStreamSynchronize(c->stream);
+        sb_dfree(c, tmp);
+        return st;
+    }
+    *out = tmp;
+    return SB_OK;
+}
+
+extern "C" sb_status sb_cloud_state(sb_ctx* c, int64_t idx, uint64_t* bits_out)
+{
+    if (!c || !bits_out) return SB_ERR_ARG;
+    uint64_t* tmp = nullptr;
+    SB_TRY(cloud_state_dev(c, idx, &tmp));
+    sb_status st = sb_copy_out(c, bits_out, tmp, sizeof(uint64_t) * (size_t)sb_cdiv(c->n, 64));
     cudaStreamSynchronize(c->stream);
     sb_dfree(c, tmp);
+    return st;
+}
+
+// Edges whose sign the state switches: bit e of word e / 64 = lab[u] ^ lab[v]
+// ^ neg of edge e (sb_graph_edges order).  One warp per 64-edge word.
+__global__ void k_switch_edges(const int2* __restrict__ edges, int64_t m, const uint64_t* __restrict__ state,
+                               uint64_t* __restrict__ out, unsigned long long* __restrict__ count)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t words = sb_cdiv(m, 64);
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < words;
+         w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        uint32_t half[2];
+        for (int h = 0; h < 2; h++) {
+            const int64_t e = 64 * w + 32 * h + lane;
+            uint32_t bit = 0;
+            if (e < m) {
+                const int2 ed = edges[e];
+                const uint32_t u = (uint32_t)ed.x, v = (uint32_t)ed.y & SB_ID_MASK;
+                bit = (uint32_t)(((state[u >> 6] >> (u & 63)) ^ (state[v >> 6] >> (v & 63))) & 1ull) ^
+                      (ed.y < 0 ? 1u : 0u);
+            }
+            half[h] = __ballot_sync(0xffffffffu, bit);
+        }
+        if (lane == 0) {
+            out[w] = ((uint64_t)half[1] << 32) | half[0];
+            atomicAdd(count, (unsigned long long)(__popc(half[0]) + __popc(half[1])));
+        }
+    }
+}
+
+extern "C" sb_status sb_cloud_switch(sb_ctx* c, int64_t idx, uint64_t* edge_bits_out, int64_t* n_switched_out)
+{
+    if (!c || !edge_bits_out) return SB_ERR_ARG;
+    uint64_t* state = nullptr;
+    SB_TRY(cloud_state_dev(c, idx, &state));
+    const int64_t words = sb_cdiv(c->m, 64);
+    uint64_t* bits = (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * (size_t)std::max<int64_t>(words, 1));
+    unsigned long long* cnt = (unsigned long long*)sb_dalloc(c, sizeof(unsigned long long));
+    sb_status st = (bits && cnt) ? SB_OK : sb_fail(c, SB_ERR_OOM, "switch export");
+    if (st == SB_OK) st = cuda_st(c, cudaMemsetAsync(cnt, 0, sizeof(*cnt), c->stream), "memset");
+    if (st == SB_OK && words > 0) {
+        const unsigned blocks = (unsigned)std::min<int64_t>(sb_cdiv(words * 32, 256), (int64_t)c->num_sms * 8);
+        k_switch_edges<<<blocks, 256, 0, c->stream>>>(c->edges, c->m, state, bits, cnt);
+        st = sb_after_launch(c, "k_switch_edges");
+    }
+    if (st == SB_OK) st = sb_copy_out(c, edge_bits_out, bits, sizeof(uint64_t) * (size_t)words);
+    unsigned long long h = 0;
+    if (st == SB_OK) st = cuda_st(c, cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, c->stream),
+                                         "count copy");
+    cudaStreamSynchronize(c->stream);
+    if (st == SB_OK && n_switched_out) *n_switched_out = (int64_t)h;
+    sb_dfree(c, state);
+    sb_dfree(c, bits);
+    sb_dfree(c, cnt);
     return st;
 }
 

@@ -198,6 +198,31 @@ def test_cloud_balanced_graph_single_state(P, sb):
     assert np.array_equal(lab, (side ^ side[0]).astype(np.int8))
 
 
+def test_cloud_switch_lists_match_oracle(P, sb):
+    """The edges each cloud state switches (the paper's output) equal the
+    oracle's lab[u] ^ lab[v] ^ neg for that state's first tree, and their
+    number is the state's S; the balanced state itself is sb_cloud_state."""
+    n, u, v, s = synth.random_connected(400, 1300, neg_frac=0.3, seed=21)
+    g = load_both(sb, n, u, v, s)
+    seed, K = 3, 130
+    sb.cloud_reset(max_states=K + 8)
+    sb.sample_trees(seed, 0, K)
+    cl, fr = sb.cloud()
+    assert len(cl["S"]) > 10
+    for i in range(len(cl["S"])):
+        bits, cnt = sb.cloud_switch(i)
+        _, _, clab, _ = O.tree(g, seed, int(cl["first_tree"][i]))
+        want = (clab[g.eu] ^ clab[g.ev] ^ (g.eneg != 0)).astype(np.uint8)
+        words = bits.cpu().numpy().view(np.uint64)
+        got = ((words[np.arange(g.m) // 64] >> (np.arange(g.m) % 64).astype(np.uint64)) & np.uint64(1)).astype(np.uint8)
+        assert np.array_equal(got, want), i
+        assert cnt == int(want.sum()) == int(cl["S"][i])
+        st = sb.cloud_state(i).cpu().numpy().view(np.uint64)
+        lab = ((st[np.arange(g.n) // 64] >> (np.arange(g.n) % 64).astype(np.uint64)) & np.uint64(1)).astype(np.uint8)
+        assert np.array_equal(lab, clab)
+    assert fr == int(cl["S"].min())
+
+
 @pytest.mark.parametrize("hash_bits", [64, 3])
 def test_cloud_accumulates_and_checks_collisions(P, sb, hash_bits):
     # a small graph with few distinct states so trees repeat states
