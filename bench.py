@@ -608,6 +608,7 @@ def batch_leg(args, P):
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.steps
     prof = sb.profile_read()
+    bfs_stats = sb.stats()
     g0 = torch.from_numpy(synth.gamma0(n_tot, R, seed=0)).cuda()
     out = torch.empty_like(g0)
     steps_gl = 100
@@ -631,6 +632,7 @@ def batch_leg(args, P):
         "states_median": float(np.median(cl["n_states"])),
         "graphl_F_median": float(np.median(F_final.cpu().numpy())),
         "tuning": tuned,
+        "bfs_stats": bfs_stats,
     }
     try:
         line["cpu_baseline"] = batch_cpu_baseline(graphs, K)

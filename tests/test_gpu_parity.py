@@ -409,3 +409,50 @@ def test_graphl_gradient_central_differences_2000_vertex_subgraph(P, sb, rmat20)
         fd[i] = gout[rr] * (Lp[rr] - Lm[rr]) / (2 * h)
     got = grad[vs, rs]
     assert np.linalg.norm(got - fd) <= 1e-5 * np.linalg.norm(fd) + 1e-7
+
+
+def test_argument_and_state_errors(P):
+    """Calls out of order and sizes out of range come back as status codes
+    (no fault, no crash), and the context stays usable afterwards."""
+    ARG, STATE = -1, -10
+    sb = P.SignedBal(0)
+    try:
+        for call in (lambda: sb.sample_trees(0, 0, 8), lambda: sb.graph_edges()):
+            with pytest.raises(P.SignedBalError) as e:
+                call()
+            assert e.value.code == STATE
+        n, u, v, s = synth.random_connected(200, 500, seed=5)
+        g = load_both(sb, n, u, v, s)
+        with pytest.raises(P.SignedBalError) as e:
+            sb.frustration()
+        assert e.value.code == STATE
+        for K in (0, 4097):
+            with pytest.raises(P.SignedBalError) as e:
+                sb.sample_trees(0, 0, K)
+            assert e.value.code == ARG
+        with pytest.raises(P.SignedBalError) as e:
+            sb.sample_trees(0, -1, 8)
+        assert e.value.code == ARG
+        for knob, val in (("bfs_words", 33), ("bfs_group", 3), ("gl_lanes", 16), ("score_blocks_sm", 99)):
+            with pytest.raises(P.SignedBalError) as e:
+                sb.set_tuning(**{knob: val})
+            assert e.value.code == ARG
+        # the largest K in one call, still exact
+        check_batch(P, sb, g, seed=2, t0=0, K=4096, parents=False)
+        sb.cloud_reset(max_states=5000)
+        cl, _ = sb.cloud()
+        with pytest.raises(P.SignedBalError) as e:
+            sb.cloud_state(len(cl["S"]))
+        assert e.value.code == ARG
+        with pytest.raises(P.SignedBalError) as e:
+            sb.cloud_switch(-1)
+        assert e.value.code == ARG
+        gam = torch.zeros((g.n, 4), device="cuda")
+        for R in (0, 65537):
+            with pytest.raises(P.SignedBalError) as e:
+                sb._check(sb.lib.sb_graphL_fwd(sb.h, P._ptr(gam), R, P._ptr(gam), None))
+            assert e.value.code == ARG
+        # still usable
+        check_batch(P, sb, g, seed=3, t0=5, K=70, parents=True)
+    finally:
+        sb.close()
