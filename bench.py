@@ -657,6 +657,11 @@ def scale_leg(args, P):
     torch.cuda.synchronize()
     ingest_s = time.perf_counter() - t
     K = 4096
+    tuned = {"default": True}
+    if not args.no_tune:
+        from paper_2311_00869_gb300 import autotune
+
+        tuned = autotune.tune(sb, K=K)
     sb.cloud_reset(max_states=(args.warmup + args.steps) * K + 64)
     counts = torch.empty(K, dtype=torch.int32, device="cuda")
     hashes = torch.empty(K, dtype=torch.int64, device="cuda")
@@ -698,7 +703,7 @@ def scale_leg(args, P):
         "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
         "roofline": roofline(prof, n1, m1, K, stats, (clk or {}).get("sm_mhz")),
         "roofline_score": roofline_family("score", prof, n1, m1, K),
-        "extras": {"fr_min": int(fr_min), "distinct_states": int(cl["S"].shape[0]), "bfs_stats": stats,
+        "extras": {"fr_min": int(fr_min), "distinct_states": int(cl["S"].shape[0]), "bfs_stats": stats, "tuning": tuned,
                    "negative_fraction": float((s < 0).mean())},
     }
     print(json.dumps(line), flush=True)
