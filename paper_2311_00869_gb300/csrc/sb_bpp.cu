@@ -643,6 +643,8 @@ __global__ void k_canon_out(const uint64_t* __restrict__ lab, int64_t total, int
 #define SC_THREADS 256
 #define SC_TILE 2048                     // edges per shared-memory tile (16 KB)
 #define SC_PLANES 12                     // ripple planes of the eights
+#define SC_FAST_BATCH 1                  // whole 8-edge batches without per-edge checks
+#define SC_RIPPLE_EXIT 1                 // stop the ripple when no carry is left
 #define SC_FLUSH ((1 << SC_PLANES) - 1)  // batches of 8 edges between flushes
 #define SC_WAIT_CYCLES (4ll * 1000 * 1000 * 1000)  // ~2 s at 2 GHz
 
@@ -687,6 +689,7 @@ struct ScoreAcc {
         uint64_t cy = eights;
 #pragma unroll
         for (int b = 0; b < SC_PLANES; b++) {
+            if (SC_RIPPLE_EXIT && !cy) break;  // carries die out after a few planes
             const uint64_t t = P[b] & cy;
             P[b] ^= cy;
             cy = t;
@@ -761,7 +764,22 @@ __global__ void __launch_bounds__(SC_THREADS, SEG ? 3 : 4) k_score(ScoreArgs A)
         const int2* te = tiles + buf * SC_TILE;
         const int cnt = (int)min((int64_t)SC_TILE, A.m - t * SC_TILE);
         if (act) {
-            for (int b = j; b < cnt; b += 8 * NGS) {
+            int b = j;
+            if (!SEG && SC_FAST_BATCH) {
+                // whole batches of 8 edges: no per-edge checks
+                for (; b + 7 * NGS < cnt; b += 8 * NGS) {
+                    uint64_t x[8];
+#pragma unroll
+                    for (int k = 0; k < 8; k++) {
+                        const int2 ed = te[b + k * NGS];
+                        const uint64_t negm = (uint64_t)(int64_t)(ed.y >> 31);
+                        x[k] = lw[(int64_t)ed.x * Wt] ^ lw[(int64_t)((uint32_t)ed.y & SB_ID_MASK) * Wt] ^ negm;
+                    }
+                    acc.add8(x);
+                    if (acc.nb == SC_FLUSH) acc.flush(dst0);
+                }
+            }
+            for (; b < cnt; b += 8 * NGS) {
                 int2 ed[8];
 #pragma unroll
                 for (int k = 0; k < 8; k++) {
