@@ -377,7 +377,7 @@ def _src_digest(paths):
 # kernel sources still match the digest taken when it was captured.
 _BPP_SRC = ("paper_2311_00869_gb300/csrc/sb_bpp.cu", "paper_2311_00869_gb300/csrc/sb_internal.cuh")
 NCU_TRAFFIC = {
-    "bfs": (3528443136 + 1342137344, _BPP_SRC, "d4bcbdcb9aac2d6c320c1c18e50e13c4176e6885244c8a1629d0931522488fb7"),
+    "bfs": (3528443136 + 1342137344, _BPP_SRC, "0ad64616a18518d84f07f4b60bc7111ebfe4a35723ed114a61b85e97c00ba857"),
 }
 
 
