@@ -106,10 +106,9 @@ sb_status sb_profile_read(sb_ctx* ctx, double* ms_out, int64_t* launches_out);
    SB_TUNE_GL_LANES          graphL lanes per row segment: 8 (32 columns)
                              or 32 (128 columns) when R % 4 == 0 (8)
    SB_TUNE_BFS_GROUP         lanes that share one vertex in the BFS, a power
-                             of two in [1, 32]: twice the launch's words
-                             rounded up to a power of two splits every row
-                             between two halves of the group; any other value
-                             (0 too) gives one lane per word
+                             of two in [1, 32]; used when it is at most twice
+                             the launch's words rounded up to a power of two
+                             (0 or otherwise: that power of two)
    Results never depend on them.  sb_get_tuning returns the current value. */
 #define SB_TUNE_BFS_WORDS 0
 #define SB_TUNE_SCORE_BLOCKS_SM 1

@@ -116,18 +116,15 @@ __device__ __forceinline__ int group_excl_scan(int x, unsigned gmask, int gl, in
 // lockstep: the 8 neighbours at once (atomicMin, then the entry equal to the
 // minimum writes its label), or, when they hold more candidates than the
 // queue, one neighbour at a time (its entries have distinct slots).
-// The group here is the G lanes of one part (see k_bfs); the part walks the
-// tiles j0, j0 + jstep, ... of the row.
 // `cur` and `lab` are rewritten between levels by other blocks, so they are
 // read with plain (coherent) loads; the column array is read-only.
 template <bool PAR, int BD, int G>
 __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint64_t* cur, const uint64_t* lab, int Wb,
                                          int Wt, int wofs, int gl, uint64_t mask, uint32_t y, uint32_t goff,
                                          const uint32_t* akey, uint32_t* best, uint8_t* labb, int32_t* bestu,
-                                         uint16_t* queue, int tid, unsigned gmask, uint64_t& once, uint32_t& nhash,
-                                         int j0 = 0, int jstep = 8)
+                                         uint16_t* queue, int tid, unsigned gmask, uint64_t& once, uint32_t& nhash)
 {
-    for (int j = j0; j < len; j += jstep) {
+    for (int j = 0; j < len; j += 8) {
         uint32_t c[8];
         uint64_t f[8], l[8];
 #pragma unroll
@@ -318,15 +315,10 @@ __device__ __forceinline__ uint64_t winner_labels(const uint8_t* labb, int tid, 
     return lx;
 }
 
-// A vertex is owned by a group of G lanes in SP parts of GW = G / SP lanes:
-// lane gl owns word gl % GW, and part gl / GW walks every SP-th tile of 8
-// neighbours with its own minima; part 0 then takes the smaller of the parts'
-// minima for every tree.
-template <int G, bool PAR, int SP>
+template <int G, bool PAR>
 __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
     k_bfs(BfsArgs A)
 {
-    constexpr int GW = G / SP;
     constexpr int BD = PAR ? BFS_THREADS_PAR : BFS_THREADS;
     extern __shared__ uint32_t smem[];
     uint32_t* akey = smem;                        // tree salts, KSLOT(word, tree)
@@ -338,10 +330,8 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
 
     const int tid = threadIdx.x;
     const int gl = tid & (G - 1);
-    const int part = gl / GW, wl = gl & (GW - 1);
-    const bool act = wl < A.Wb;     // this lane's word exists
-    const bool own = act && part == 0;  // and this lane writes its results
-    const unsigned gmask = group_mask(G), pmask = group_mask(GW);
+    const bool act = gl < A.Wb;
+    const unsigned gmask = group_mask(G);
     const int64_t groups_total = (int64_t)gridDim.x * (BD / G);
     const int64_t group_id = (int64_t)blockIdx.x * (BD / G) + tid / G;
     const unsigned nblocks = gridDim.x;
@@ -352,8 +342,8 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
     __syncthreads();
 
     const int Wb = A.Wb, Wt = A.Wt, w0 = A.w0;
-    const int wofs = w0 + wl;
-    uint16_t* queue = queues + (tid / GW) * (BFS_QUEUE_PER_LANE * GW);
+    const int wofs = w0 + gl;
+    uint16_t* queue = queues + (tid / G) * (BFS_QUEUE_PER_LANE * G);
     uint32_t n_scan = 0, n_hash = 0, n_hash_hub = 0;  // work counters
     int L = 1;
     while (true) {
@@ -374,7 +364,7 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
                 const int32_t v = itm.v;
                 const int32_t d = A.done[v];
                 if (d >= 0 && L >= d + 3) continue;
-                const uint64_t vis_w = act ? A.vis[(int64_t)v * Wb + wl] : ~0ull;
+                const uint64_t vis_w = act ? A.vis[(int64_t)v * Wb + gl] : ~0ull;
                 const uint64_t U = ~vis_w;
                 const int32_t* cp = A.col + itm.beg;
                 const int len = itm.end - itm.beg;
@@ -385,42 +375,19 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
                 if (__any_sync(gmask, U != 0)) {
                     const uint32_t goff = A.vgoff ? (uint32_t)A.vgoff[v] : 0u;
                     const uint32_t y = sb_child_salt(A.S, (uint32_t)v - goff);
-                    if (U && part == 0) n_scan += (uint32_t)len;
+                    if (U) n_scan += (uint32_t)len;
                     // one pass: every candidate of every open tree is hashed (a
                     // first pass that singled out the trees with two or more
                     // candidates cost more than the few hashes it saved)
                     best_reset<BD>(best, tid, U);
-                    scan_row<PAR, BD, GW>(cp, len, cur, A.lab, Wb, Wt, wofs, wl, U, y, goff, akey, best, labb, bestu,
-                                          queue, tid, pmask, once, hub ? n_hash_hub : n_hash, 8 * part, 8 * SP);
-                    if (SP > 1) {
-                        // part 0 keeps the smaller minimum of every tree
-                        __syncwarp(gmask);
-#pragma unroll
-                        for (int q = 1; q < SP; q++) {
-                            const uint64_t oq = __shfl_sync(gmask, once, gl + q * GW, G);
-                            if (part == 0) {
-                                for (uint64_t b = oq; b;) {
-                                    const int t = __ffsll((long long)b) - 1;
-                                    b &= b - 1;
-                                    const int src = tid + q * GW;
-                                    const uint32_t hq = best[BSLOT(src, t)];
-                                    if (hq < best[BSLOT(tid, t)]) {
-                                        best[BSLOT(tid, t)] = hq;
-                                        labb[LSLOT(tid, t)] = labb[LSLOT(src, t)];
-                                        if (PAR) bestu[BSLOT(tid, t)] = bestu[BSLOT(src, t)];
-                                    }
-                                }
-                                once |= oq;
-                            }
-                        }
-                        __syncwarp(gmask);
-                    }
+                    scan_row<PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, goff, akey, best, labb, bestu,
+                                         queue, tid, gmask, once, hub ? n_hash_hub : n_hash);
                     labx = winner_labels<BD>(labb, tid, once);
                 }
                 if (hub) {
                     // chunk of a split row: publish the chunk minima, one atomic per tree
-                    if (own && once) {
-                        uint64_t* hb = A.hubbest + ((int64_t)itm.hub * Wb + wl) * 64;
+                    if (once) {
+                        uint64_t* hb = A.hubbest + ((int64_t)itm.hub * Wb + gl) * 64;
                         for (uint64_t b = once; b;) {
                             const int t = __ffsll((long long)b) - 1;
                             b &= b - 1;
@@ -429,27 +396,27 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
                                                            ((labx >> t) & 1ull);
                             atomicMin((unsigned long long*)(hb + t), key);
                         }
-                        atomicOr((unsigned long long*)(A.hubnew + (int64_t)itm.hub * Wb + wl), once);
+                        atomicOr((unsigned long long*)(A.hubnew + (int64_t)itm.hub * Wb + gl), once);
                     }
                     continue;
                 }
-                if (PAR && A.parents && part == 0) {
+                if (PAR && A.parents) {
                     for (uint64_t b = once; b;) {
                         const int t = __ffsll((long long)b) - 1;
                         b &= b - 1;
                         A.parents[(64 * (int64_t)wofs + t) * A.n + v] = bestu[BSLOT(tid, t)];
                     }
                 }
-                if (own) {
+                if (act) {
                     if (once) {
                         A.lab[(int64_t)v * Wt + wofs] |= labx & once;
-                        A.vis[(int64_t)v * Wb + wl] = vis_w | once;
+                        A.vis[(int64_t)v * Wb + gl] = vis_w | once;
                         any_new = true;
                     }
-                    nxt[(int64_t)v * Wb + wl] = once;
+                    nxt[(int64_t)v * Wb + gl] = once;
                 }
                 if (d < 0) {
-                    const bool full = part != 0 || (vis_w | once) == ~0ull;
+                    const bool full = (vis_w | once) == ~0ull;
                     const bool all = __all_sync(gmask, full);
                     if (all && gl == 0) A.done[v] = L;
                 }
@@ -464,13 +431,13 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
                 const int32_t d = A.done[v];
                 if (d >= 0 && L >= d + 3) continue;
                 uint64_t nw = 0, vis_w = ~0ull;
-                if (own) {
-                    vis_w = A.vis[(int64_t)v * Wb + wl];
-                    uint64_t* hn = A.hubnew + h * Wb + wl;
+                if (act) {
+                    vis_w = A.vis[(int64_t)v * Wb + gl];
+                    uint64_t* hn = A.hubnew + h * Wb + gl;
                     nw = *hn & ~vis_w;
                     *hn = 0;
                     uint64_t labx = 0;
-                    uint64_t* hb = A.hubbest + (h * Wb + wl) * 64;
+                    uint64_t* hb = A.hubbest + (h * Wb + gl) * 64;
                     for (uint64_t b = nw; b;) {
                         const int t = __ffsll((long long)b) - 1;
                         b &= b - 1;
@@ -482,10 +449,10 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
                     }
                     if (nw) {
                         A.lab[(int64_t)v * Wt + wofs] |= labx;
-                        A.vis[(int64_t)v * Wb + wl] = vis_w | nw;
+                        A.vis[(int64_t)v * Wb + gl] = vis_w | nw;
                         any_new = true;
                     }
-                    nxt[(int64_t)v * Wb + wl] = nw;
+                    nxt[(int64_t)v * Wb + gl] = nw;
                 }
                 if (d < 0) {
                     const bool all = __all_sync(gmask, (vis_w | nw) == ~0ull);
@@ -684,24 +651,15 @@ static int group_for(int Wb)
 }
 
 template <bool PAR>
-static const void* bfs_kernel(int G, int SP)
+static const void* bfs_kernel(int G)
 {
-    if (SP == 2) {
-        switch (G) {
-        case 2: return (const void*)k_bfs<2, PAR, 2>;
-        case 4: return (const void*)k_bfs<4, PAR, 2>;
-        case 8: return (const void*)k_bfs<8, PAR, 2>;
-        case 16: return (const void*)k_bfs<16, PAR, 2>;
-        default: return (const void*)k_bfs<32, PAR, 2>;
-        }
-    }
     switch (G) {
-    case 1: return (const void*)k_bfs<1, PAR, 1>;
-    case 2: return (const void*)k_bfs<2, PAR, 1>;
-    case 4: return (const void*)k_bfs<4, PAR, 1>;
-    case 8: return (const void*)k_bfs<8, PAR, 1>;
-    case 16: return (const void*)k_bfs<16, PAR, 1>;
-    default: return (const void*)k_bfs<32, PAR, 1>;
+    case 1: return (const void*)k_bfs<1, PAR>;
+    case 2: return (const void*)k_bfs<2, PAR>;
+    case 4: return (const void*)k_bfs<4, PAR>;
+    case 8: return (const void*)k_bfs<8, PAR>;
+    case 16: return (const void*)k_bfs<16, PAR>;
+    default: return (const void*)k_bfs<32, PAR>;
     }
 }
 
@@ -719,11 +677,9 @@ static sb_status run_bfs(sb_ctx* c, int w0, int Wb, int32_t* parents)
     const bool par = parents != nullptr;
     // lanes beyond the launch's words still share the hash rounds
     const int Gw = group_for(Wb), Gt = (int)c->tune[SB_TUNE_BFS_GROUP];
-    // a group twice as wide as the words splits every row between two parts
-    const int G = (Gt == 2 * Gw && Gt <= 32) ? Gt : Gw;
-    const int SP = G / Gw;
+    const int G = (Gt > Gw && Gt <= 2 * Gw) ? Gt : Gw;  // widened at most twofold
     const int BD = par ? BFS_THREADS_PAR : BFS_THREADS;
-    const void* fn = par ? bfs_kernel<true>(G, SP) : bfs_kernel<false>(G, SP);
+    const void* fn = par ? bfs_kernel<true>(G) : bfs_kernel<false>(G);
     size_t smem = sizeof(uint32_t) * ((size_t)Wb * 65 + 65 * BD) + 68 * BD + sizeof(uint16_t) * BFS_QUEUE_PER_LANE * BD +
                   (par ? sizeof(int32_t) * 65 * BD : 0);
     SB_CHECK_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

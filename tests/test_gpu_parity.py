@@ -135,20 +135,6 @@ def test_split_rows_hub(P, sb):
     check_batch(P, sb, g, seed=6, t0=0, K=2048 + 33, parents=False)
 
 
-@pytest.mark.parametrize("K,words", [(130, 3), (1024 + 33, 16), (2048, 32)])
-def test_split_groups_match_oracle(P, sb, K, words):
-    """Groups twice as wide as the words of a launch (every row split between
-    two halves that merge their minima) give the same trees, parents and
-    labels; the hub graph also exercises split rows."""
-    n, a, b, s = _hub_graph(seed=78, n=1500, extra=3000, neg=0.3)
-    g = load_both(sb, n, a, b, s)
-    gw = 1
-    while gw < min(words, 32):
-        gw *= 2
-    sb.set_tuning(bfs_words=words, bfs_group=min(32, 2 * gw))
-    check_batch(P, sb, g, seed=12, t0=3, K=K, parents=K <= 1100)
-
-
 def test_config1_plain_equals_batched_and_oracle(P, sb):
     n, u, v, s = synth.er_graph()
     g = load_both(sb, n, u, v, s)
