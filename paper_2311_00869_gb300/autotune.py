@@ -3,7 +3,7 @@
 It times the candidate values on the loaded graph with the library's own
 CUDA-event profiler and keeps the fastest per knob:
   bfs_words        64-tree words grown per BFS launch (trees per launch / 64)
-  bfs_group        lanes sharing one vertex in the BFS (the words, or 32)
+  bfs_group        lanes sharing one vertex in the BFS (the words, or twice that)
   score_blocks_sm  blocks per SM of the frustration scorer
   gl_lanes         graphL lanes per row segment (8 -> 32 columns, 32 -> 128)
 Choices are cached in JSON per (GPU name, graph shape bucket, K, R), so a
@@ -86,7 +86,7 @@ def tune(sb, K: int = 1024, R: int | None = None, seed: int = 987654321, reps: i
     while g0 < best[1]:
         g0 <<= 1
     best = None
-    for g in sorted({g0, 32}):
+    for g in sorted({g0, min(32, 2 * g0)}):  # the library widens a group at most twofold
         sb.set_tuning(bfs_group=g)
         t = _time_family(sb, "bfs", sample, reps)
         if best is None or t < best[0]:
