@@ -643,6 +643,31 @@ def batch_leg(args, P):
     return 0
 
 
+def scale_cpu_baseline(sb, n, u, v, s, K, each=8):
+    """The oracle on trees [0, each) and [K - each, K) of the paper-scale
+    graph on all host cores (the rate is extrapolated to all K trees), and a
+    bit-for-bit check of those trees' counts and hashes against the GPU."""
+    import oracle as O
+
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    g = O.clean_graph(n, u, v, s)
+    clean_s = time.perf_counter() - t
+    trees = list(range(each)) + list(range(K - each, K))
+    t = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        refs = list(ex.map(lambda tt: O.sample(g, SEED, tt, 1, want_labels=False), trees))
+    el = time.perf_counter() - t
+    sb.sample_trees(SEED, 0, K)
+    counts, hashes = sb.frustration()
+    counts, hashes = counts.cpu().numpy(), hashes.cpu().numpy().view(np.uint64)
+    same = all(counts[tt] == r["counts"][0] and hashes[tt] == r["hashes"][0] for tt, r in zip(trees, refs))
+    return {"value": len(trees) * g.m / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"trees [0,{each}) and [{K - each},{K}) on {cores} threads, {el:.1f} s "
+                      f"(rate extrapolated to {K} trees); cleaning the graph took {clean_s:.1f} s",
+            "bit_exact_on_sample": bool(same)}
+
+
 def scale_leg(args, P):
     """Paper-scale graphBpp: R-MAT with 2^24 vertex ids and 2^27 distinct
     undirected edges, three planted factions (94.8 / 2.6 / 2.6 %, inter-faction
@@ -706,6 +731,11 @@ def scale_leg(args, P):
         "extras": {"fr_min": int(fr_min), "distinct_states": int(cl["S"].shape[0]), "bfs_stats": stats, "tuning": tuned,
                    "negative_fraction": float((s < 0).mean())},
     }
+    if not args.no_extras:
+        try:
+            line["cpu_baseline"] = scale_cpu_baseline(sb, n, u, v, s, K)
+        except Exception as e:  # the baseline must not hide the main number
+            line["cpu_baseline"] = {"error": repr(e)}
     print(json.dumps(line), flush=True)
     sb.close()
     return 0
