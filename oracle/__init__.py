@@ -72,6 +72,7 @@ def lib():
                 "or_state_hash": (u64, [i64, P]),
                 "or_sample": (ctypes.c_int, [i64, P, P, P, i64, P, P, P, u64, i64, i64, P, P, P, P]),
                 "or_cloud": (i64, [i64, i64, i64, P, P, P, P, P, P]),
+                "or_cloud_bounded": (i64, [i64, i64, i64, P, P, i64, P, P, P, P]),
                 "or_graphl_loss_f64": (None, [i64, P, P, P, P, i64, P, P]),
                 "or_graphl_grad_f64": (None, [i64, P, P, P, P, i64, P, P]),
                 "or_graphl_grad_f32": (None, [i64, P, P, P, P, i64, P, P]),
@@ -182,6 +183,22 @@ def cloud(labels, counts, t0=0):
     S = np.zeros(max(K, 1), np.int32)
     H = np.zeros(max(K, 1), np.uint64)
     ns = lib().or_cloud(n, K, t0, _p(labels), _p(counts), _p(first), _p(cnt), _p(S), _p(H))
+    if ns < 0:
+        raise OracleError(int(ns))
+    return {"first_tree": first[:ns], "count": cnt[:ns], "S": S[:ns], "H": H[:ns]}
+
+
+def cloud_bounded(labels, counts, fmax, t0=0):
+    """Cloud of the scalable variant (at most fmax states; see or_cloud_bounded)."""
+    labels = _c(labels, np.uint8)
+    counts = _c(counts, np.int32)
+    K, n = labels.shape
+    cap = max(1, min(int(fmax), K))
+    first = np.zeros(cap, np.int64)
+    cnt = np.zeros(cap, np.int32)
+    S = np.zeros(cap, np.int32)
+    H = np.zeros(cap, np.uint64)
+    ns = lib().or_cloud_bounded(n, K, t0, _p(labels), _p(counts), int(fmax), _p(first), _p(cnt), _p(S), _p(H))
     if ns < 0:
         raise OracleError(int(ns))
     return {"first_tree": first[:ns], "count": cnt[:ns], "S": S[:ns], "H": H[:ns]}

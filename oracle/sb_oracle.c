@@ -457,6 +457,84 @@ int64_t or_cloud(int64_t n, int64_t K, int64_t t0, const uint8_t* clab, const in
     return ns;
 }
 
+/*
+ * Frustration cloud of the scalable variant (appendix "Scaling graphBpp for
+ * Large Signed Graphs", the algorithm alg-scale): at most fmax states are
+ * kept.  Trees are taken in order.  The first tree's state is stored.  After
+ * that a tree is used only when its S is below the largest stored S: a state
+ * already stored gets its count raised; a new state is appended while fewer
+ * than fmax are stored, and otherwise takes the place of the stored state
+ * with the largest S (the printed argmin would throw away the best state, so
+ * it is read as argmax; among equal S the lowest slot goes).  A stored state's
+ * first tree is the tree that stored it.  Output: the stored states ordered by
+ * that tree.  Returns their number.
+ */
+int64_t or_cloud_bounded(int64_t n, int64_t K, int64_t t0, const uint8_t* clab, const int32_t* counts, int64_t fmax,
+                         int64_t* first_out, int32_t* count_out, int32_t* S_out, uint64_t* H_out)
+{
+    if (fmax < 1) return OR_ERR_ARG;
+    int64_t cap = fmax < K ? fmax : (K > 0 ? K : 1);
+    int64_t* rep = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap);
+    int32_t* S = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
+    int32_t* cnt = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
+    if (!rep || !S || !cnt) {
+        free(rep); free(S); free(cnt);
+        return OR_ERR_OOM;
+    }
+    int64_t ns = 0;
+    for (int64_t i = 0; i < K; i++) {
+        if (ns == 0) {
+            rep[0] = i;
+            S[0] = counts[i];
+            cnt[0] = 1;
+            ns = 1;
+            continue;
+        }
+        int32_t maxS = S[0];
+        int64_t arg = 0;
+        for (int64_t j = 1; j < ns; j++)
+            if (S[j] > maxS) {
+                maxS = S[j];
+                arg = j;
+            }
+        if (!(counts[i] < maxS)) continue;
+        int64_t found = -1;
+        for (int64_t j = 0; j < ns && found < 0; j++)
+            if (memcmp(clab + rep[j] * n, clab + i * n, (size_t)n) == 0) found = j;
+        if (found >= 0) {
+            cnt[found]++;
+        } else {
+            int64_t slot = ns < fmax ? ns++ : arg;
+            rep[slot] = i;
+            S[slot] = counts[i];
+            cnt[slot] = 1;
+        }
+    }
+    /* order of the storing tree (insertion sort: ns is small) */
+    int64_t* ord = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ns > 0 ? ns : 1));
+    if (!ord) {
+        free(rep); free(S); free(cnt);
+        return OR_ERR_OOM;
+    }
+    for (int64_t j = 0; j < ns; j++) {
+        int64_t k = j;
+        while (k > 0 && rep[ord[k - 1]] > rep[j]) {
+            ord[k] = ord[k - 1];
+            k--;
+        }
+        ord[k] = j;
+    }
+    for (int64_t a = 0; a < ns; a++) {
+        int64_t j = ord[a];
+        first_out[a] = t0 + rep[j];
+        count_out[a] = cnt[j];
+        S_out[a] = S[j];
+        H_out[a] = or_state_hash(n, clab + rep[j] * n);
+    }
+    free(ord); free(rep); free(S); free(cnt);
+    return ns;
+}
+
 /* ------------------------------------------------------------------ graphL */
 
 /*

@@ -298,6 +298,59 @@ def _small_graph(oracle, seed=5):
     return oracle.clean_graph(n, u, v, s)
 
 
+def _scalable_case(O, K=400, seed=17):
+    n, u, v, s = synth.random_connected(120, 260, neg_frac=0.35, seed=seed)
+    g = O.clean_graph(n, u, v, s)
+    smp = O.sample(g, 5, 0, K)
+    return smp, O.cloud(smp["labels"], smp["counts"])
+
+
+def test_scalable_cloud_without_eviction_follows_the_first_state(oracle):
+    """With room for every state, the scalable cloud (appendix algorithm
+    alg-scale) holds the first tree's state, counted once (its repeats are
+    not below the largest stored S), followed by every state whose S is below
+    it with all its trees, in order of first appearance; nothing else.
+    Derived from the unbounded cloud."""
+    smp, full = _scalable_case(oracle)
+    K = smp["counts"].shape[0]
+    b = oracle.cloud_bounded(smp["labels"], smp["counts"], fmax=K)
+    s0 = int(full["S"][0])
+    keep = full["S"] < s0
+    assert full["first_tree"][0] == 0
+    assert b["first_tree"].tolist() == [0] + full["first_tree"][keep].tolist()
+    assert b["count"].tolist() == [1] + full["count"][keep].tolist()
+    assert b["S"].tolist() == [s0] + full["S"][keep].tolist()
+    assert np.array_equal(b["H"], np.concatenate([full["H"][:1], full["H"][keep]]))
+    assert keep.sum() >= 3  # the case exercises the rule
+
+
+def test_scalable_cloud_single_slot_keeps_the_first_minimum(oracle):
+    """fmax = 1: the one slot ends with the first tree whose S is the minimum
+    over all trees, counted once."""
+    smp, _ = _scalable_case(oracle, seed=18)
+    b = oracle.cloud_bounded(smp["labels"], smp["counts"], fmax=1)
+    c = smp["counts"]
+    assert b["S"].tolist() == [int(c.min())]
+    assert b["first_tree"].tolist() == [int(np.argmin(c))]
+    assert b["count"].tolist() == [1]
+
+
+@pytest.mark.parametrize("fmax", [2, 5, 17])
+def test_scalable_cloud_with_eviction_invariants(oracle, fmax):
+    """With eviction: at most fmax states, all of them states of the
+    unbounded cloud with no more trees than there, and the minimum S over
+    all trees always kept (the evicted state is one with the largest S)."""
+    smp, full = _scalable_case(oracle, seed=19)
+    b = oracle.cloud_bounded(smp["labels"], smp["counts"], fmax=fmax)
+    assert 1 <= len(b["S"]) <= fmax
+    assert int(b["S"].min()) == int(smp["counts"].min())
+    by_h = {int(h): (int(c), int(s_)) for h, c, s_ in zip(full["H"], full["count"], full["S"])}
+    for h, c, s_ in zip(b["H"], b["count"], b["S"]):
+        assert int(h) in by_h
+        assert c <= by_h[int(h)][0] and s_ == by_h[int(h)][1]
+    assert len(b["S"]) == fmax  # the case fills the cloud, so eviction happened
+
+
 def test_graphl_gradient_central_differences(oracle):
     g = _small_graph(oracle)
     R = 3
