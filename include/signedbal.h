@@ -240,6 +240,19 @@ sb_status sb_cloud(sb_ctx* ctx, sb_cloud_entry* out, int64_t cap, int64_t* n_sta
    collision path; exported hashes stay full. */
 sb_status sb_cloud_reset(sb_ctx* ctx, int64_t max_states, int32_t hash_bits);
 
+/* Empties the cloud and switches it to the scalable rule of the paper's
+   appendix algorithm for large graphs (alg-scale), with room for f_max states
+   (1 <= f_max <= 2^30): trees are taken in order; the first stored state opens
+   the cloud; after that a tree counts only when its S is below the largest
+   stored S, raising the count of its stored state, or else adding its state
+   while fewer than f_max are stored, or else replacing a stored state of
+   largest S (the paper's argmin there would replace the best state; the
+   lowest index among equal S goes).  A state's first_tree is the tree that
+   stored it.  Trees that do not count are not errors (no SB_ERR_CLOUD_FULL);
+   two different states with one 64-bit hash give SB_ERR_DEVICE_CHECK.
+   sb_cloud_reset returns to the unbounded cloud. */
+sb_status sb_cloud_reset_scalable(sb_ctx* ctx, int64_t f_max);
+
 /* Canonical labels of cloud state `idx` (order of sb_cloud), bit-packed:
    bits_out[v / 64] bit (v % 64) = label of vertex v.  ceil(n/64) words,
    host or device. */

@@ -218,6 +218,11 @@ class SignedBal:
     def cloud_reset(self, max_states=0, hash_bits=0):
         self._check(self.lib.sb_cloud_reset(self.h, max_states, hash_bits))
 
+    def cloud_reset_scalable(self, f_max):
+        """Empties the cloud and keeps at most f_max states by the paper's
+        scalable rule (see sb_cloud_reset_scalable)."""
+        self._check(self.lib.sb_cloud_reset_scalable(self.h, int(f_max)))
+
     def cloud_switch(self, idx):
         """(bits, count): int64 words with bit e set for every edge (order of
         graph_edges) that cloud state `idx` switches, and their number (= S)."""

@@ -39,6 +39,7 @@ SIGNATURES = {
     "sb_frustration": (i32, [P, P, P]),
     "sb_cloud": (i32, [P, P, i64, ctypes.POINTER(i64), ctypes.POINTER(i32)]),
     "sb_cloud_reset": (i32, [P, i64, i32]),
+    "sb_cloud_reset_scalable": (i32, [P, i64]),
     "sb_cloud_state": (i32, [P, i64, P]),
     "sb_cloud_switch": (i32, [P, i64, P, ctypes.POINTER(i64)]),
     "sb_graphL_fwd": (i32, [P, P, i32, P, P]),

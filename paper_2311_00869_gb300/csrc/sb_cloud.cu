@@ -73,6 +73,109 @@ __global__ void k_cloud_assign(const uint64_t* __restrict__ hashes, const int32_
     meta[0] = ns;
 }
 
+// true when h lies in the cyclic interval (i, j] of a table of `slots` slots
+__device__ __forceinline__ bool cl_in_cyc(uint64_t h, uint64_t i, uint64_t j)
+{
+    return i < j ? (h > i && h <= j) : (h > i || h <= j);
+}
+
+// Removes state st (key `key`) from the linear-probing table, moving later
+// entries of the same run back (no tombstones).
+__device__ void cl_table_erase(sb_cloud_slot* table, int64_t slots, uint64_t key, int32_t st)
+{
+    const uint64_t mask = (uint64_t)(slots - 1);
+    uint64_t hole = cl_slot_of(key, slots);
+    for (int64_t p = 0; p < slots && table[hole].state != st; p++) hole = (hole + 1) & mask;
+    if (table[hole].state != st) return;
+    uint64_t j = hole;
+    for (int64_t p = 0; p < slots; p++) {
+        j = (j + 1) & mask;
+        if (table[j].state < 0) break;
+        const uint64_t home = cl_slot_of(table[j].key, slots);
+        if (!cl_in_cyc(home, hole, j)) {
+            table[hole] = table[j];
+            hole = j;
+        }
+    }
+    table[hole].state = -1;
+}
+
+// The scalable rule (appendix algorithm alg-scale; the replaced state is one
+// of largest S, the lowest such index): sequential in tree order.  The first
+// stored state opens the cloud; later trees count only when their S is below
+// the largest stored S; a new state is appended while fewer than fmax are
+// stored, else it takes the slot of a largest-S state.  A replaced state that
+// trees of this batch had matched loses those matches (assign = -1).
+__global__ void k_cloud_assign_scalable(const uint64_t* __restrict__ hashes, const int32_t* __restrict__ counts,
+                                        int64_t K, int64_t tree_begin, sb_cloud_slot* table, int64_t slots,
+                                        sb_cloud_entry* entries, int64_t fmax, int32_t* meta, int32_t* assign,
+                                        int32_t* rep, int32_t* touch, int32_t* mismatch)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int32_t ns = meta[0];
+    int32_t maxS = 0, arg = -1;
+    auto rescan = [&]() {
+        arg = -1;
+        for (int32_t j = 0; j < ns; j++)
+            if (arg < 0 || entries[j].S > maxS) {
+                maxS = entries[j].S;
+                arg = j;
+            }
+    };
+    rescan();
+    const uint64_t mask = (uint64_t)(slots - 1);
+    for (int64_t i = 0; i < K; i++) {
+        mismatch[i] = 0;
+        assign[i] = -1;
+        const uint64_t h = hashes[i];
+        if (ns > 0 && !(counts[i] < maxS)) continue;
+        uint64_t s = cl_slot_of(h, slots);
+        int32_t found = -1;
+        for (int64_t p = 0; p < slots && table[s].state >= 0; p++) {
+            if (table[s].key == h) {
+                found = table[s].state;
+                break;
+            }
+            s = (s + 1) & mask;
+        }
+        if (found >= 0) {
+            entries[found].count += 1;
+            assign[i] = found;
+            touch[found] = 1;
+            if (entries[found].S != counts[i]) mismatch[i] = 1;  // certainly another state
+            continue;
+        }
+        int32_t st;
+        if (ns < fmax) {
+            st = ns++;
+        } else {
+            st = arg;
+            cl_table_erase(table, slots, entries[st].hash, st);
+            if (touch[st])
+                for (int64_t j = 0; j < i; j++)
+                    if (assign[j] == st) {
+                        assign[j] = -1;
+                        mismatch[j] = 0;
+                    }
+            s = cl_slot_of(h, slots);  // the erase may have moved entries
+            for (int64_t p = 0; p < slots && table[s].state >= 0; p++) s = (s + 1) & mask;
+        }
+        table[s].key = h;
+        table[s].state = st;
+        sb_cloud_entry e;
+        e.hash = h;
+        e.S = counts[i];
+        e.count = 1;
+        e.first_tree = tree_begin + i;
+        entries[st] = e;
+        rep[st] = (int32_t)i;
+        touch[st] = 1;
+        assign[i] = st;
+        if (st == arg || ns == 1) rescan();  // a replacement, or the first state
+    }
+    meta[0] = ns;
+}
+
 // Canonical label bit of batch tree i at vertex v.
 __device__ __forceinline__ uint32_t cl_bit(const uint64_t* row, const uint64_t* flipw, int64_t i)
 {
@@ -174,8 +277,9 @@ sb_status sb_cloud_alloc(sb_ctx* c)
     c->cl_assign = (int32_t*)sb_dalloc(c, sizeof(int32_t) * SB_TREES_MAX);
     c->cl_rep = (int32_t*)sb_dalloc(c, sizeof(int32_t) * (size_t)c->cl_max);
     c->cl_mismatch = (int32_t*)sb_dalloc(c, sizeof(int32_t) * SB_TREES_MAX);
+    c->cl_touch = (int32_t*)sb_dalloc(c, sizeof(int32_t) * (size_t)c->cl_max);
     if (!c->cl_table || !c->cl_entries || !c->cl_bits || !c->cl_meta || !c->cl_assign || !c->cl_rep ||
-        !c->cl_mismatch) {
+        !c->cl_mismatch || !c->cl_touch) {
         sb_release_cloud(c);
         return sb_fail(c, SB_ERR_OOM, "cloud storage (%lld states)", (long long)c->cl_max);
     }
@@ -274,10 +378,18 @@ sb_status sb_cloud_insert_batch(sb_ctx* c)
     SB_TRY(sb_score_batch(c));
     SB_CHECK_CUDA(c, cudaMemsetAsync(c->cl_rep, 0xFF, sizeof(int32_t) * (size_t)c->cl_max, c->stream));
     SbProf prof(c, SB_PROF_CLOUD);
-    k_cloud_assign<<<1, 32, 0, c->stream>>>(c->hashes, c->counts, c->K, c->tree_begin, c->cl_hash_bits, c->cl_table,
-                                            c->cl_slots, c->cl_entries, c->cl_max, c->cl_meta, c->cl_assign, c->cl_rep,
-                                            c->cl_mismatch);
-    SB_TRY(sb_after_launch(c, "k_cloud_assign"));
+    if (c->cl_fmax > 0) {
+        SB_CHECK_CUDA(c, cudaMemsetAsync(c->cl_touch, 0, sizeof(int32_t) * (size_t)c->cl_max, c->stream));
+        k_cloud_assign_scalable<<<1, 32, 0, c->stream>>>(c->hashes, c->counts, c->K, c->tree_begin, c->cl_table,
+                                                         c->cl_slots, c->cl_entries, c->cl_fmax, c->cl_meta,
+                                                         c->cl_assign, c->cl_rep, c->cl_touch, c->cl_mismatch);
+        SB_TRY(sb_after_launch(c, "k_cloud_assign_scalable"));
+    } else {
+        k_cloud_assign<<<1, 32, 0, c->stream>>>(c->hashes, c->counts, c->K, c->tree_begin, c->cl_hash_bits,
+                                                c->cl_table, c->cl_slots, c->cl_entries, c->cl_max, c->cl_meta,
+                                                c->cl_assign, c->cl_rep, c->cl_mismatch);
+        SB_TRY(sb_after_launch(c, "k_cloud_assign"));
+    }
     const int64_t nchunks = sb_cdiv(c->n, 64);
     size_t smem = sizeof(uint64_t) * 64 * (size_t)c->W;
     if (smem > 48 * 1024)
@@ -291,7 +403,12 @@ sb_status sb_cloud_insert_batch(sb_ctx* c)
     int32_t meta[4];
     SB_CHECK_CUDA(c, cudaMemcpyAsync(meta, c->cl_meta, sizeof(meta), cudaMemcpyDeviceToHost, c->stream));
     SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (meta[2] > 0) SB_TRY(cloud_resolve_collisions(c));
+    if (meta[2] > 0) {
+        // a 64-bit hash shared by two different states: resolved exactly by the
+        // unbounded cloud; the scalable one reports it instead
+        if (c->cl_fmax > 0) return sb_fail(c, SB_ERR_DEVICE_CHECK, "state hash collision in the scalable cloud");
+        SB_TRY(cloud_resolve_collisions(c));
+    }
     c->batch_in_cloud = true;
     return SB_OK;
 }
@@ -304,8 +421,17 @@ extern "C" sb_status sb_cloud_reset(sb_ctx* c, int64_t max_states, int32_t hash_
     sb_release_cloud(c);
     c->cl_max = max_states > 0 ? max_states : CL_DEFAULT_STATES;
     c->cl_hash_bits = hash_bits > 0 ? hash_bits : 64;
+    c->cl_fmax = 0;
     c->batch_in_cloud = true;  // a reset starts from the next sampled batch
     if (c->has_graph) SB_TRY(sb_cloud_alloc(c));
+    return SB_OK;
+}
+
+extern "C" sb_status sb_cloud_reset_scalable(sb_ctx* c, int64_t f_max)
+{
+    if (!c || f_max < 1 || f_max > (1ll << 30)) return SB_ERR_ARG;
+    SB_TRY(sb_cloud_reset(c, f_max, 64));
+    c->cl_fmax = f_max;
     return SB_OK;
 }
 

@@ -208,6 +208,7 @@ void sb_release_cloud(sb_ctx* c)
     SB_FREE(cl_assign);
     SB_FREE(cl_rep);
     SB_FREE(cl_mismatch);
+    SB_FREE(cl_touch);
     c->cl_slots = 0;
     c->cl_n_host = 0;
     c->cl_order.clear();

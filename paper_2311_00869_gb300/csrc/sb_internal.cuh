@@ -149,6 +149,8 @@ struct sb_ctx {
     int32_t* cl_assign = nullptr;  // K: state per tree of the batch
     int32_t* cl_rep = nullptr;     // cl_max: batch tree that created the state in this batch, else -1
     int32_t* cl_mismatch = nullptr;// K
+    int32_t* cl_touch = nullptr;   // cl_max: 1 when the state was matched or stored in this batch
+    int64_t cl_fmax = 0;           // > 0: the scalable rule with at most cl_fmax states
     int64_t cl_n_host = 0;
     std::vector<int32_t> cl_order;  // output position -> state index (by first tree)
 

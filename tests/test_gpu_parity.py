@@ -198,6 +198,33 @@ def test_cloud_balanced_graph_single_state(P, sb):
     assert np.array_equal(lab, (side ^ side[0]).astype(np.int8))
 
 
+@pytest.mark.parametrize("fmax", [1, 5, 17, 400])
+def test_scalable_cloud_matches_oracle(P, sb, fmax):
+    """The scalable cloud over three sampling calls (130 + 130 + 140 trees)
+    equals the oracle's on all 400 trees: same states, counts, S, first trees
+    and hashes, in the same order; its states export like any other."""
+    n, u, v, s = synth.random_connected(120, 260, neg_frac=0.35, seed=17)
+    g = load_both(sb, n, u, v, s)
+    sb.cloud_reset_scalable(fmax)
+    t0 = 0
+    for K in (130, 130, 140):
+        sb.sample_trees(5, t0, K)
+        sb.cloud_insert()
+        t0 += K
+    cl, fr = sb.cloud()
+    ref = O.sample(g, 5, 0, t0)
+    rc = O.cloud_bounded(ref["labels"], ref["counts"], fmax)
+    assert np.array_equal(cl["first_tree"], rc["first_tree"])
+    assert np.array_equal(cl["count"], rc["count"])
+    assert np.array_equal(cl["S"], rc["S"])
+    assert np.array_equal(cl["hash"], rc["H"])
+    assert fr == int(rc["S"].min())
+    for i in range(len(cl["S"])):
+        st = sb.cloud_state(i).cpu().numpy().view(np.uint64)
+        lab = ((st[np.arange(g.n) // 64] >> (np.arange(g.n) % 64).astype(np.uint64)) & np.uint64(1)).astype(np.uint8)
+        assert np.array_equal(lab, ref["labels"][int(cl["first_tree"][i])])
+
+
 def test_cloud_switch_lists_match_oracle(P, sb):
     """The edges each cloud state switches (the paper's output) equal the
     oracle's lab[u] ^ lab[v] ^ neg for that state's first tree, and their
