@@ -50,9 +50,10 @@ def parse():
     ap.add_argument("--scale", type=int, default=None, help="R-MAT scale (default 20; 24 for --leg scale24)")
     ap.add_argument("--edges-log2", type=int, default=None, help="log2 of the edge count (default 24; 27)")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain / graphL / e2e / cpu legs")
-    ap.add_argument("--leg", default="bpp", choices=["bpp", "graphl", "batch", "scale24"],
+    ap.add_argument("--leg", default="bpp", choices=["bpp", "graphl", "batch", "scale24", "quality"],
                     help="bpp: the graphBpp line (default); graphl: graphL descent only; batch: uneven batch; "
-                         "scale24: R-MAT 2^24 vertices / 2^27 edges, 4096 trees per step")
+                         "scale24: R-MAT 2^24 vertices / 2^27 edges, 4096 trees per step; "
+                         "quality: graphBpp min S and graphL min F against the planted state")
     ap.add_argument("--R", type=int, default=256, help="graphL start points (--leg graphl)")
     ap.add_argument("--gl-steps", type=int, default=500, help="graphL descent steps (--leg graphl)")
     ap.add_argument("--graphs", type=int, default=4096, help="graphs in the uneven batch (--leg batch)")
@@ -238,6 +239,8 @@ def main():
         return batch_leg(args, P)
     if args.leg == "scale24":
         return scale_leg(args, P)
+    if args.leg == "quality":
+        return quality_leg(args, P)
     n, u, v, s = workload(args)
     stream = torch.cuda.current_stream()
     sb = P.SignedBal(local, stream=stream)
@@ -638,6 +641,60 @@ def batch_leg(args, P):
         line["cpu_baseline"] = batch_cpu_baseline(graphs, K)
     except Exception as e:  # the baseline must not hide the main number
         line["cpu_baseline"] = {"error": repr(e)}
+    print(json.dumps(line), flush=True)
+    sb.close()
+    return 0
+
+
+def quality_leg(args, P, K_total=4096, R=256, steps=500, alpha=0.05):
+    """graphL against graphBpp on the 2^20 two-faction graph: the smallest S
+    among the first K trees (K = 64 ... 4096) and distinct states, the
+    smallest graphL F among the first r start points (r = 1, 16, 256) after
+    every 50 steps, and the frustration of the planted two-faction state."""
+    import torch
+
+    import synth
+
+    n, u, v, s, fac = synth.rmat_two_faction(scale=args.scale, m_target=1 << args.edges_log2, with_factions=True)
+    sb = P.SignedBal(0)
+    n1, m1, vmap = sb.load_graph(n, u, v, s, want_vmap=True)
+    if not args.no_tune:
+        from paper_2311_00869_gb300 import autotune
+
+        autotune.tune(sb, K=TREES, R=R)
+    # planted state on the cleaned graph: edges whose sign disagrees with it
+    cu, cv, cneg = (t.cpu().numpy() for t in sb.graph_edges())
+    inv = np.empty(n1, np.int64)
+    inv[vmap[vmap >= 0]] = np.nonzero(vmap >= 0)[0]
+    planted = int(np.count_nonzero((fac[inv[cu]] * fac[inv[cv]] < 0) != (cneg != 0)))
+    sb.cloud_reset(max_states=K_total + 64)
+    mins, counts_all = {}, []
+    t0 = 0
+    while t0 < K_total:
+        sb.sample_trees(SEED, t0, TREES)
+        c, _ = sb.frustration()
+        counts_all.append(c.cpu().numpy())
+        sb.cloud_insert()
+        t0 += TREES
+    cs = np.concatenate(counts_all)
+    for k in (64, 256, 1024, 4096):
+        if k <= K_total:
+            mins[str(k)] = int(cs[:k].min())
+    cl, fr = sb.cloud()
+    g0 = torch.from_numpy(synth.gamma0(n1, R, seed=0)).cuda()
+    _, _, F_trace, F_final = sb.graphL_descent(g0, alpha, steps, trace=True)
+    Ft = F_trace.cpu().numpy()
+    Ff = F_final.cpu().numpy()
+    gl = {}
+    for r in (1, 16, 256):
+        if r <= R:
+            gl[str(r)] = [int(Ft[st, :r].min()) for st in range(0, steps, 50)] + [int(Ff[:r].min())]
+    line = {"leg": "quality", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n1, "m": m1, "graphl_R": R, "graphl_steps": steps,
+                       "graphl_alpha": alpha},
+            "planted_state_frustration": planted,
+            "graphbpp_min_S_after_K_trees": mins, "graphbpp_distinct_states": int(cl["S"].shape[0]),
+            "graphl_min_F_every_50_steps_then_final_by_start_points": gl}
     print(json.dumps(line), flush=True)
     sb.close()
     return 0

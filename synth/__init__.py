@@ -80,15 +80,17 @@ def rmat_edges(scale, m_target, abcd=(0.57, 0.19, 0.19, 0.05), seed=1002):
     return n, perm[u], perm[v], rng
 
 
-def rmat_two_faction(scale=20, m_target=1 << 24, noise=0.10, seed=1002):
+def rmat_two_faction(scale=20, m_target=1 << 24, noise=0.10, seed=1002, with_factions=False):
     """Planted two-faction balance (faction iid 50/50, sign = product of the
-    faction signs) followed by iid sign flips with probability `noise`."""
+    faction signs) followed by iid sign flips with probability `noise`.
+    with_factions=True also returns the planted faction (+1 / -1) of every
+    vertex."""
     n, u, v, rng = rmat_edges(scale, m_target, seed=seed)
     fac = np.where(rng.random(n) < 0.5, 1, -1).astype(np.int8)
     sign = (fac[u] * fac[v]).astype(np.int8)
     flip = rng.random(u.shape[0]) < noise
     sign[flip] = -sign[flip]
-    return n, u, v, sign
+    return (n, u, v, sign, fac) if with_factions else (n, u, v, sign)
 
 
 RMAT_CHUNK = 1 << 22
