@@ -14,6 +14,7 @@
 #include "sb_internal.cuh"
 
 #define CL_DEFAULT_STATES 4096
+#define CL_PARALLEL_ASSIGN 1  // one-block sorted assignment instead of the sequential pass
 
 __host__ __device__ __forceinline__ uint64_t cl_slot_of(uint64_t key, int64_t slots)
 {
@@ -71,6 +72,150 @@ __global__ void k_cloud_assign(const uint64_t* __restrict__ hashes, const int32_
         }
     }
     meta[0] = ns;
+}
+
+// The same assignment as k_cloud_assign, by one block: the batch's (key,
+// tree) pairs are sorted, each run of one key is led by its smallest tree;
+// leaders look their key up in the table; keys not found become new states,
+// numbered in the order of their leaders' trees (what the sequential pass
+// gives), and are inserted with atomicCAS on empty slots (no lookups run
+// while they are inserted, and the keys are distinct).
+#define CLP_THREADS 1024
+__global__ void __launch_bounds__(CLP_THREADS)
+    k_cloud_assign_par(const uint64_t* __restrict__ hashes, const int32_t* __restrict__ counts, int K,
+                       int64_t tree_begin, int hash_bits, sb_cloud_slot* table, int64_t slots, sb_cloud_entry* entries,
+                       int64_t max_states, int32_t* meta, int32_t* assign, int32_t* rep, int32_t* mismatch)
+{
+    extern __shared__ __align__(16) unsigned char clp_smem[];
+    int P = 1;
+    while (P < K) P <<= 1;
+    uint64_t* key = (uint64_t*)clp_smem;       // P sorted keys
+    int32_t* idx = (int32_t*)(key + P);        // P trees, sorted with the keys
+    int32_t* runst = idx + P;                  // K: state of the run at each sorted position
+    int32_t* isnew = runst + K;                // K, by tree: 1 for a leader of a new key; then its new index
+    __shared__ int32_t s_part[CLP_THREADS / 32], s_ns, s_total;
+    const int tid = threadIdx.x;
+    const uint64_t mask = (uint64_t)(slots - 1);
+    if (tid == 0) s_ns = meta[0];
+    for (int i = tid; i < P; i += CLP_THREADS) {
+        key[i] = i < K ? cl_key(hashes[i], hash_bits) : ~0ull;
+        idx[i] = i < K ? i : 0x7FFFFFFF;
+    }
+    for (int i = tid; i < K; i += CLP_THREADS) isnew[i] = 0;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < P; i += CLP_THREADS) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const bool up = (i & k) == 0;
+                    const bool gt = key[i] > key[p] || (key[i] == key[p] && idx[i] > idx[p]);
+                    if (gt == up) {
+                        const uint64_t tk = key[i];
+                        key[i] = key[p];
+                        key[p] = tk;
+                        const int32_t ti = idx[i];
+                        idx[i] = idx[p];
+                        idx[p] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    // leaders look their key up; -2 marks a key to create
+    for (int i = tid; i < K; i += CLP_THREADS) {
+        if (i > 0 && key[i] == key[i - 1]) continue;
+        uint64_t s = cl_slot_of(key[i], slots);
+        int32_t found = -1;
+        for (int64_t p = 0; p < slots && table[s].state >= 0; p++) {
+            if (table[s].key == key[i]) {
+                found = table[s].state;
+                break;
+            }
+            s = (s + 1) & mask;
+        }
+        runst[i] = found >= 0 ? found : -2;
+        if (found < 0) isnew[idx[i]] = 1;
+    }
+    __syncthreads();
+    // new indices in tree order: exclusive prefix of isnew over the trees
+    {
+        const int per = (K + CLP_THREADS - 1) / CLP_THREADS;
+        const int b = tid * per, e = min(K, b + per);
+        int32_t sum = 0;
+        for (int t = b; t < e; t++) sum += isnew[t];
+        int32_t inc = sum;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+            if ((tid & 31) >= d) inc += y;
+        }
+        if ((tid & 31) == 31) s_part[tid >> 5] = inc;
+        __syncthreads();
+        if (tid < 32) {
+            int32_t w = tid < CLP_THREADS / 32 ? s_part[tid] : 0;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, w, d);
+                if (tid >= d) w += y;
+            }
+            if (tid < CLP_THREADS / 32) s_part[tid] = w;
+            if (tid == 31) s_total = w;
+        }
+        __syncthreads();
+        int32_t run = (tid >= 32 ? s_part[(tid >> 5) - 1] : 0) + inc - sum;
+        for (int t = b; t < e; t++) {
+            const int32_t f = isnew[t];
+            isnew[t] = f ? s_ns + run : -1;  // the new state's index (may exceed capacity)
+            run += f;
+        }
+    }
+    __syncthreads();
+    // leaders of new keys: create and insert (or overflow)
+    for (int i = tid; i < K; i += CLP_THREADS) {
+        if (runst[i] != -2) continue;
+        const int32_t tl = idx[i];
+        const int32_t st = isnew[tl];
+        if (st >= max_states) {
+            runst[i] = -1;
+            continue;
+        }
+        uint64_t s = cl_slot_of(key[i], slots);
+        for (int64_t p = 0; p < slots; p++) {
+            if (atomicCAS(&table[s].state, -1, st) == -1) {
+                table[s].key = key[i];
+                break;
+            }
+            s = (s + 1) & mask;
+        }
+        sb_cloud_entry en;
+        en.hash = hashes[tl];
+        en.S = counts[tl];
+        en.count = 0;
+        en.first_tree = tree_begin + tl;
+        entries[st] = en;
+        rep[st] = tl;
+        runst[i] = st;
+    }
+    __syncthreads();
+    // every head hands its state to the rest of its run
+    for (int i = tid; i < K; i += CLP_THREADS) {
+        if (i > 0 && key[i] == key[i - 1]) continue;
+        for (int j = i + 1; j < K && key[j] == key[i]; j++) runst[j] = runst[i];
+    }
+    __syncthreads();
+    // every tree: the state of its run, counts, overflow, S check
+    for (int i = tid; i < K; i += CLP_THREADS) {
+        const int32_t st = runst[i];
+        const int32_t t = idx[i];
+        assign[t] = st;
+        mismatch[t] = 0;
+        if (st < 0) {
+            atomicAdd(&meta[1], 1);
+            continue;
+        }
+        atomicAdd(&entries[st].count, 1);
+        if (entries[st].S != counts[t]) mismatch[t] = 1;  // certainly another state
+    }
+    if (tid == 0) meta[0] = (int32_t)min((int64_t)s_ns + s_total, max_states);
 }
 
 // true when h lies in the cyclic interval (i, j] of a table of `slots` slots
@@ -384,6 +529,17 @@ sb_status sb_cloud_insert_batch(sb_ctx* c)
                                                          c->cl_slots, c->cl_entries, c->cl_fmax, c->cl_meta,
                                                          c->cl_assign, c->cl_rep, c->cl_touch, c->cl_mismatch);
         SB_TRY(sb_after_launch(c, "k_cloud_assign_scalable"));
+    } else if (CL_PARALLEL_ASSIGN) {
+        int P = 1;
+        while (P < c->K) P <<= 1;
+        const size_t smem = (sizeof(uint64_t) + sizeof(int32_t)) * (size_t)P + 2 * sizeof(int32_t) * (size_t)c->K;
+        SB_CHECK_CUDA(c, cudaFuncSetAttribute(k_cloud_assign_par, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+        k_cloud_assign_par<<<1, CLP_THREADS, smem, c->stream>>>(c->hashes, c->counts, (int)c->K, c->tree_begin,
+                                                                c->cl_hash_bits, c->cl_table, c->cl_slots,
+                                                                c->cl_entries, c->cl_max, c->cl_meta, c->cl_assign,
+                                                                c->cl_rep, c->cl_mismatch);
+        SB_TRY(sb_after_launch(c, "k_cloud_assign_par"));
     } else {
         k_cloud_assign<<<1, 32, 0, c->stream>>>(c->hashes, c->counts, c->K, c->tree_begin, c->cl_hash_bits,
                                                 c->cl_table, c->cl_slots, c->cl_entries, c->cl_max, c->cl_meta,
