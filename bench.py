@@ -380,7 +380,7 @@ def _src_digest(paths):
 # kernel sources still match the digest taken when it was captured.
 _BPP_SRC = ("paper_2311_00869_gb300/csrc/sb_bpp.cu", "paper_2311_00869_gb300/csrc/sb_internal.cuh")
 NCU_TRAFFIC = {
-    "bfs": (3528443136 + 1342137344, _BPP_SRC, "0ad64616a18518d84f07f4b60bc7111ebfe4a35723ed114a61b85e97c00ba857"),
+    "bfs": (3528688640 + 1342480896, _BPP_SRC, "cfd350523d37e5cf0ba9cbf5b6c26b69ef8d31c21f2a69ef1599980461598d91"),
 }
 
 

@@ -489,52 +489,26 @@ struct BatchIn {
     const int64_t* eofs;
 };
 
-// The scorer's copy of the edges: every edge from its colder endpoint (lower
-// degree; on a tie, the larger id) to its hotter one, ordered by (colder,
-// hotter).  CSR rows list their neighbours in increasing id, so the row of c
-// filtered to its hotter neighbours is exactly c's run of that order: a count
-// per row, a scan, and an ordered compaction (one warp per row) build it.
-__device__ __forceinline__ bool sc_hotter(uint32_t h, int64_t c, int32_t dc, const int32_t* __restrict__ deg)
+// key of the scorer's copy of an edge: (colder << (nb + 1)) | (hotter << 1) | neg,
+// colder = the endpoint of lower degree (on a tie, the larger id)
+__global__ void k_orient_keys(const int2* __restrict__ edges, int64_t m, const int32_t* __restrict__ deg, int nb,
+                              uint64_t* __restrict__ keys)
 {
-    const int32_t dh = deg[h];
-    return dh > dc || (dh == dc && (int64_t)h < c);
-}
-
-__global__ void k_sc_count(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                           const int32_t* __restrict__ deg, int64_t n, int32_t* __restrict__ cnt)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n; c += nw) {
-        const int32_t b = rowptr[c], e = rowptr[c + 1], dc = deg[c];
-        uint32_t k = 0;
-        for (int32_t j = b + lane; j < e; j += 32) k += sc_hotter((uint32_t)col[j] & SB_ID_MASK, c, dc, deg) ? 1u : 0u;
-        k = __reduce_add_sync(0xffffffffu, k);
-        if (lane == 0) cnt[c] = (int32_t)k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int2 ed = edges[e];
+        const uint32_t u = (uint32_t)ed.x, v = (uint32_t)ed.y & SB_ID_MASK;
+        const bool u_cold = deg[u] < deg[v];  // u < v, so a tie makes v the colder one
+        const uint64_t cold = u_cold ? u : v, hot = u_cold ? v : u;
+        keys[e] = (cold << (nb + 1)) | (hot << 1) | (uint64_t)(ed.y < 0 ? 1 : 0);
     }
 }
 
-__global__ void k_sc_fill(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                          const int32_t* __restrict__ deg, int64_t n, const int32_t* __restrict__ first,
-                          int2* __restrict__ out)
+__global__ void k_emit_sc_edges(const uint64_t* __restrict__ keys, int64_t m, int nb, int2* __restrict__ out)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n; c += nw) {
-        const int32_t b = rowptr[c], e = rowptr[c + 1], dc = deg[c];
-        int32_t pos = first[c];
-        for (int32_t j0 = b; j0 < e; j0 += 32) {
-            const int32_t j = j0 + lane;
-            uint32_t cc = 0;
-            bool p = false;
-            if (j < e) {
-                cc = (uint32_t)col[j];
-                p = sc_hotter(cc & SB_ID_MASK, c, dc, deg);
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, p);
-            if (p) out[pos + __popc(bal & ((1u << lane) - 1u))] = make_int2((int32_t)c, (int32_t)cc);
-            pos += __popc(bal);
-        }
+    const uint64_t idm = (1ull << nb) - 1ull;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = keys[e];
+        out[e] = make_int2((int32_t)(k >> (nb + 1)), (int32_t)((uint32_t)((k >> 1) & idm) | ((uint32_t)(k & 1ull) << 31)));
     }
 }
 
@@ -707,13 +681,11 @@ static sb_status load_graph_impl(sb_ctx* c, int64_t n, int64_t m, const int32_t*
     if (!c->sc_edges) return sb_fail(c, SB_ERR_OOM, "graph storage");
     SB_CHECK_CUDA(c, cudaMemsetAsync(c->sc_edges + m2, 0, 2 * sizeof(int2), c->stream));
     if (m2 > 0) {
-        // low and lfirst are free again: counts and first positions per row
-        const unsigned gw = (unsigned)std::min<int64_t>(sb_cdiv(n1 * 32, 256), (int64_t)c->num_sms * 32);
-        k_sc_count<<<gw, 256, 0, c->stream>>>(c->rowptr, c->col, deg, n1, low);
-        SB_TRY(sb_after_launch(c, "k_sc_count"));
-        SB_TRY(sb_scan_i32(c, low, lfirst, n1, nullptr));
-        k_sc_fill<<<gw, 256, 0, c->stream>>>(c->rowptr, c->col, deg, n1, lfirst, c->sc_edges);
-        SB_TRY(sb_after_launch(c, "k_sc_fill"));
+        k_orient_keys<<<gm2, 256, 0, c->stream>>>(c->edges, m2, deg, nb2, lkeys);
+        SB_TRY(sb_after_launch(c, "k_orient_keys"));
+        SB_TRY(sb_radix_sort_u64(c, lkeys, m2, 2 * nb2 + 1));
+        k_emit_sc_edges<<<gm2, 256, 0, c->stream>>>(lkeys, m2, nb2, c->sc_edges);
+        SB_TRY(sb_after_launch(c, "k_emit_sc_edges"));
     }
     if (B) {
         const int64_t G = B->G;
