@@ -8,7 +8,8 @@ experiments (Sec. 5-6, Tables of dataset sizes), which are not available here:
 R-MAT and Chung-Lu give their power-law degree shape, and the planted faction
 structure plus iid sign noise gives their mostly-positive sign mix.
 
-Every generator returns (n, src int32[m], dst int32[m], sign int8[m]).
+Every generator returns (n, src int32[m], dst int32[m], sign int8[m]) (the two-faction
+R-MAT can add the planted factions).
 """
 from __future__ import annotations
 
