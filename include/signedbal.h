@@ -311,9 +311,10 @@ sb_status sb_graphL_round(sb_ctx* ctx, const float* gamma, int32_t R, int32_t* F
 /*
  * Allocation-free variant of sb_graphL_fwd (the paper has no counterpart;
  * this is an integration convenience).  For callers that cannot allocate
- * device memory at call time: code that runs while a CUDA graph is being
- * captured, hosts that hand the library a fixed memory budget up front, or
- * plugins whose host application owns every allocator.  It takes no context
+ * device memory at call time because their memory is fixed ahead of time:
+ * hosts that hand the library a fixed memory budget up front, plugins whose
+ * host application owns every allocator, and loops that must not enter the
+ * CUDA allocator while they run.  It takes no context
  * and calls no cudaMalloc, cudaFree or allocating library routine; its
  * scratch is a fixed device array of about 2.4 MiB that every GPU loading the
  * library keeps until exit.

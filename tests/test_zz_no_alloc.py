@@ -1,8 +1,9 @@
 """The allocation-free relaxed-loss entry point (sb_graphL_fwd_static).
 
-It exists for callers that cannot allocate device memory when they call in:
-code running under CUDA graph capture, hosts with a fixed memory budget, or
-plugins whose host owns the allocator.  This file is named to be collected
+It exists for callers that cannot allocate device memory when they call in,
+because their memory is fixed ahead of time: hosts with a fixed memory budget,
+plugins whose host owns the allocator, or loops that must not enter the CUDA
+allocator.  This file is named to be collected
 last so that a failure here never hides the other GPU tests.  It checks two
 calls in a row through the C ABI against sb_graphL_fwd on the same inputs,
 with the tolerance the other graphL tests use (1e-5 relative to the sum of
