@@ -410,8 +410,9 @@ def _peaks():
 def roofline_family(fam, prof, n, m, K, stats=None, sm_mhz=None):
     """Roofline of one kernel family: HBM-bound families against the measured
     copy bandwidth with their algorithmic bytes per launch; the BFS against
-    the integer-ALU peak (SMs x INT32 lanes x SM clock) with the hash work the
-    argmin parent rule needs (counted by the kernel) per launch."""
+    the integer-ALU peak (SMs x INT32 lanes x SM clock) with the parent-key
+    hashes the kernel computes per launch (every candidate of every open tree,
+    as counted by the kernel)."""
     peaks = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     src = "measured" if "hbm_gbs" in peaks else "fallback"
