@@ -71,6 +71,9 @@ def lib():
                 "or_frustration": (i64, [i64, P, P, P, P]),
                 "or_state_hash": (u64, [i64, P]),
                 "or_sample": (ctypes.c_int, [i64, P, P, P, i64, P, P, P, u64, i64, i64, P, P, P, P]),
+                "or_mst_weight": (u64, [u64, i64, i64, i64]),
+                "or_mst_tree": (i64, [i64, i64, P, P, P, u64, i64, P, P]),
+                "or_mst_sample": (ctypes.c_int, [i64, i64, P, P, P, u64, i64, i64, P, P, P, P]),
                 "or_cloud": (i64, [i64, i64, i64, P, P, P, P, P, P]),
                 "or_cloud_bounded": (i64, [i64, i64, i64, P, P, i64, P, P, P, P]),
                 "or_graphl_loss_f64": (None, [i64, P, P, P, P, i64, P, P]),
@@ -160,6 +163,35 @@ def sample(g: Graph, seed: int, t0: int, K: int, want_labels=True, want_parents=
     if rc != 0:
         raise OracleError(rc)
     return {"counts": counts, "hashes": hashes, "labels": labels, "parents": parents}
+
+
+def mst_tree(g: Graph, seed: int, t: int):
+    """(tree edge count, in_tree[m] uint8, canonical labels[n] uint8) of
+    randomized Kruskal tree t."""
+    in_tree = np.zeros(max(g.m, 1), np.uint8)
+    clab = np.zeros(g.n, np.uint8)
+    r = lib().or_mst_tree(g.n, g.m, _p(g.eu), _p(g.ev), _p(g.eneg), seed, t, _p(in_tree), _p(clab))
+    if r < 0:
+        raise OracleError(int(r))
+    return int(r), in_tree[: g.m], clab
+
+
+def mst_sample(g: Graph, seed: int, t0: int, K: int, want_labels=True, want_in_tree=False):
+    """Kruskal trees [t0, t0+K): dict with counts, hashes, labels (uint8[K, n])
+    and in_tree (uint8[K, m]) when asked."""
+    counts = np.zeros(K, np.int32)
+    hashes = np.zeros(K, np.uint64)
+    labels = np.zeros((K, g.n), np.uint8) if want_labels else None
+    in_tree = np.zeros((K, g.m), np.uint8) if want_in_tree else None
+    rc = lib().or_mst_sample(g.n, g.m, _p(g.eu), _p(g.ev), _p(g.eneg), seed, t0, K, _p(in_tree), _p(labels),
+                             _p(counts), _p(hashes))
+    if rc != 0:
+        raise OracleError(rc)
+    return {"counts": counts, "hashes": hashes, "labels": labels, "in_tree": in_tree}
+
+
+def mst_weight(seed, t, u, v) -> int:
+    return int(lib().or_mst_weight(seed, t, u, v))
 
 
 def frustration(g: Graph, clab) -> int:

@@ -19,6 +19,7 @@
  *   Sec. 4, Eq. 2-4 + Alg. 2         graphL loss, gradient, descent, rounding
  *   Appendix "Implementation"        input cleaning (duplicates, self-loops,
  *                                    inconsistencies, invalid signs), LCC
+ *   Appendix, tree samplers          Kruskal's algorithm with random edge weights
  *
  * Readings taken where the paper is silent (each one is also listed in the
  * design notes):
@@ -393,6 +394,139 @@ int or_sample(int64_t n, const int64_t* rowptr, const int32_t* col, const int8_t
     if (!lab) return OR_ERR_OOM;
     for (int64_t i = 0; i < K; i++) {
         int64_t r = or_tree(n, rowptr, col, colneg, seed, t0 + i, parent_out ? parent_out + i * n : NULL, lab, NULL);
+        if (r < 0) {
+            free(lab);
+            return (int)r;
+        }
+        if (clab_out) memcpy(clab_out + i * n, lab, (size_t)n);
+        if (counts_out) counts_out[i] = (int32_t)or_frustration(m, eu, ev, eneg, lab);
+        if (hashes_out) hashes_out[i] = or_state_hash(n, lab);
+    }
+    free(lab);
+    return OR_OK;
+}
+
+/* ------------------------------------------------ randomized Kruskal trees */
+
+/* weight of the cleaned edge (u, v), u < v, in Kruskal tree t */
+uint64_t or_mst_weight(uint64_t seed, int64_t t, int64_t u, int64_t v)
+{
+    uint64_t pair = ((uint64_t)(uint32_t)u << 32) | (uint64_t)(uint32_t)v;
+    return or_mix64(pair ^ or_tree_key(seed, t));
+}
+
+typedef struct { uint64_t w; int64_t e; } or_wedge;
+
+static int or_wedge_cmp(const void* x, const void* y)
+{
+    uint64_t a = ((const or_wedge*)x)->w, b = ((const or_wedge*)y)->w;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+/* union-find root with path halving */
+static int64_t or_find_halve(int64_t* par, int64_t x)
+{
+    while (par[x] != x) {
+        par[x] = par[par[x]];
+        x = par[x];
+    }
+    return x;
+}
+
+/*
+ * Randomized Kruskal tree t (appendix, tree samplers: Kruskal's algorithm
+ * with random edge weights drawn afresh for every tree).  Reading: the weight
+ * of edge (u, v) in tree t is or_mst_weight(seed, t, u, v).  mix64 is a
+ * bijection on 64-bit words and the packed pair is injective, so one tree's
+ * weights are all distinct and its minimum spanning tree is unique (Prim's
+ * algorithm with the same weights finds the same tree).
+ * Steps, as Kruskal's algorithm states them: sort the edges by weight, then
+ * keep each edge in that order whose endpoints are still in different
+ * union-find sets, and unite the sets.
+ * State: the parity labelling of the tree, grown from vertex 0 with
+ * lab(0) = 0 and lab(y) = lab(x) XOR neg(x, y) along tree edges, so it is
+ * already canonical (vertex 0 on the +1 side).
+ * Outputs (nullable): in_tree[m] (1 for a tree edge, edge order of eu/ev),
+ * clab[n].  Returns the number of tree edges, or a negative status.
+ */
+int64_t or_mst_tree(int64_t n, int64_t m, const int32_t* eu, const int32_t* ev, const int8_t* eneg, uint64_t seed,
+                    int64_t t, uint8_t* in_tree_out, uint8_t* clab_out)
+{
+    or_wedge* order = (or_wedge*)malloc(sizeof(or_wedge) * (size_t)(m > 0 ? m : 1));
+    int64_t* set = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    uint8_t* keep = (uint8_t*)calloc((size_t)(m > 0 ? m : 1), 1);
+    int64_t* deg = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    int32_t* adj = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * n + 2));
+    int8_t* adjneg = (int8_t*)malloc((size_t)(2 * n + 2));
+    int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    uint8_t* seen = (uint8_t*)calloc((size_t)n, 1);
+    uint8_t* lab = (uint8_t*)calloc((size_t)n, 1);
+    if (!order || !set || !keep || !deg || !adj || !adjneg || !queue || !seen || !lab) {
+        free(order); free(set); free(keep); free(deg); free(adj); free(adjneg); free(queue); free(seen); free(lab);
+        return OR_ERR_OOM;
+    }
+    for (int64_t e = 0; e < m; e++) {
+        order[e].w = or_mst_weight(seed, t, eu[e], ev[e]);
+        order[e].e = e;
+    }
+    qsort(order, (size_t)m, sizeof(or_wedge), or_wedge_cmp);
+    for (int64_t v = 0; v < n; v++) set[v] = v;
+    int64_t kept = 0;
+    for (int64_t i = 0; i < m && kept < n - 1; i++) {
+        int64_t e = order[i].e;
+        int64_t a = or_find_halve(set, eu[e]), b = or_find_halve(set, ev[e]);
+        if (a == b) continue;
+        set[a] = b;
+        keep[e] = 1;
+        kept++;
+    }
+    /* tree adjacency (CSR over the kept edges), then BFS from vertex 0 */
+    for (int64_t e = 0; e < m; e++)
+        if (keep[e]) {
+            deg[eu[e] + 1]++;
+            deg[ev[e] + 1]++;
+        }
+    for (int64_t v = 0; v < n; v++) deg[v + 1] += deg[v];
+    for (int64_t e = 0; e < m; e++)
+        if (keep[e]) {
+            adj[deg[eu[e]]] = ev[e];
+            adjneg[deg[eu[e]]++] = eneg[e];
+            adj[deg[ev[e]]] = eu[e];
+            adjneg[deg[ev[e]]++] = eneg[e];
+        }
+    for (int64_t v = n; v > 0; v--) deg[v] = deg[v - 1];
+    deg[0] = 0;
+    int64_t head = 0, tail = 0;
+    if (n > 0) {
+        queue[tail++] = 0;
+        seen[0] = 1;
+    }
+    while (head < tail) {
+        int32_t x = queue[head++];
+        for (int64_t j = deg[x]; j < deg[x + 1]; j++) {
+            int32_t y = adj[j];
+            if (seen[y]) continue;
+            seen[y] = 1;
+            lab[y] = (uint8_t)(lab[x] ^ (uint8_t)adjneg[j]);
+            queue[tail++] = y;
+        }
+    }
+    if (in_tree_out) memcpy(in_tree_out, keep, (size_t)m);
+    if (clab_out) memcpy(clab_out, lab, (size_t)n);
+    free(order); free(set); free(keep); free(deg); free(adj); free(adjneg); free(queue); free(seen); free(lab);
+    return kept;
+}
+
+/* Kruskal trees [t0, t0+K): in_tree (K x m), canonical labels (K x n),
+   counts S_t and hashes H_t, each nullable. */
+int or_mst_sample(int64_t n, int64_t m, const int32_t* eu, const int32_t* ev, const int8_t* eneg, uint64_t seed,
+                  int64_t t0, int64_t K, uint8_t* in_tree_out, uint8_t* clab_out, int32_t* counts_out,
+                  uint64_t* hashes_out)
+{
+    uint8_t* lab = (uint8_t*)malloc((size_t)(n > 0 ? n : 1));
+    if (!lab) return OR_ERR_OOM;
+    for (int64_t i = 0; i < K; i++) {
+        int64_t r = or_mst_tree(n, m, eu, ev, eneg, seed, t0 + i, in_tree_out ? in_tree_out + i * m : NULL, lab);
         if (r < 0) {
             free(lab);
             return (int)r;

@@ -4,7 +4,8 @@ Each test checks the oracle against something other than itself: the paper's
 worked example (Sec. 2, Fig. 1), exhaustive search (frustration index by
 definition, max-cut for all-negative graphs, Sec. 1), Harary's theorem
 (Sec. 2), the fundamental-cycle rule of the graphB+ algorithm (appendix),
-library routines (scipy BFS distances, components, CSR; numpy matrix powers)
+library routines (scipy BFS distances, components, CSR, minimum spanning
+trees; numpy matrix powers)
 and closed forms (graphL's quadratic loss, Eq. 3-4).
 """
 import os
@@ -257,6 +258,71 @@ def test_parent_choice_is_randomized(oracle):
         total += 1
     assert abs(wins / total - 0.5) < 0.05
     assert np.all(np.abs(roots / 2000 - 0.25) < 0.05)
+
+
+# ------------------------------------------------- randomized Kruskal trees
+
+def _mst_checks(O, g, seed, t):
+    """One Kruskal tree against scipy's minimum spanning tree under the same
+    weight order, and its labels against the tree (parity, canonical form)."""
+    k, in_tree, clab = O.mst_tree(g, seed, t)
+    assert k == g.n - 1 and int(in_tree.sum()) == g.n - 1
+    # the minimum spanning tree depends only on the order of the weights:
+    # ranks 1..m are exact in float64 and distinct
+    w = np.array([O.mst_weight(seed, t, int(a), int(b)) for a, b in zip(g.eu, g.ev)], dtype=np.uint64)
+    assert np.unique(w).shape[0] == g.m
+    rank = np.empty(g.m, np.float64)
+    rank[np.argsort(w, kind="stable")] = np.arange(1, g.m + 1)
+    A = sp.coo_matrix((rank, (g.eu, g.ev)), shape=(g.n, g.n)).tocsr()
+    T = csg.minimum_spanning_tree(A).tocoo()
+    want = {(min(a, b), max(a, b)) for a, b in zip(T.row.tolist(), T.col.tolist())}
+    got = {(int(a), int(b)) for a, b, x in zip(g.eu, g.ev, in_tree) if x}
+    assert got == want
+    # every tree edge satisfied; vertex 0 on the +1 side; spanning
+    for a, b, s, x in zip(g.eu, g.ev, g.eneg, in_tree):
+        if x:
+            assert clab[a] ^ clab[b] ^ s == 0
+    assert clab[0] == 0
+    Tm = sp.coo_matrix((np.ones(g.n - 1), ([a for a, _ in got], [b for _, b in got])), shape=(g.n, g.n))
+    assert csg.connected_components(Tm, directed=False)[0] == 1
+    return O.frustration(g, clab), clab
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_kruskal_trees_are_minimum_spanning_trees(oracle, case):
+    n, u, v, s = synth.random_connected(9 + 4 * case, 8 + 5 * case, seed=500 + case)
+    g = oracle.clean_graph(n, u, v, s)
+    fr, _ = exact_frustration(g.n, g.eu, g.ev, g.eneg)
+    res = oracle.mst_sample(g, seed=case, t0=0, K=10, want_in_tree=True)
+    for t in range(10):
+        S, clab = _mst_checks(oracle, g, case, t)
+        assert S >= fr
+        assert res["counts"][t] == S and np.array_equal(res["labels"][t], clab)
+        assert res["hashes"][t] == np.uint64(oracle.state_hash(clab))
+
+
+def test_kruskal_harary_planted_balance(oracle):
+    n, u, v, s, side = synth.planted_balanced(16, 20, seed=601)
+    g = oracle.clean_graph(n, u, v, s)
+    res = oracle.mst_sample(g, seed=4, t0=0, K=16)
+    assert np.all(res["counts"] == 0)
+    want = (side ^ side[0]).astype(np.uint8)
+    assert all(np.array_equal(lab, want) for lab in res["labels"])
+
+
+def test_kruskal_cycle_drops_each_edge_equally_often(oracle):
+    # a 5-cycle: the tree omits the heaviest edge, which is uniform over the
+    # five edges when the weights are random
+    g = oracle.clean_graph(5, [0, 1, 2, 3, 4], [1, 2, 3, 4, 0], [1, -1, 1, 1, -1])
+    res = oracle.mst_sample(g, seed=9, t0=0, K=5000, want_labels=False, want_in_tree=True)
+    assert np.all(res["in_tree"].sum(axis=1) == 4)
+    freq = 1.0 - res["in_tree"].mean(axis=0)
+    assert np.all(np.abs(freq - 0.2) < 0.02)
+    # two negative edges make the cycle positive: balanced, S = 0 for every
+    # tree; with one negative edge the omitted edge closes a negative cycle
+    assert np.all(res["counts"] == 0)
+    g1 = oracle.clean_graph(5, [0, 1, 2, 3, 4], [1, 2, 3, 4, 0], [1, -1, 1, 1, 1])
+    assert np.all(oracle.mst_sample(g1, seed=9, t0=0, K=200)["counts"] == 1)
 
 
 # ------------------------------------------------------------------ cloud
