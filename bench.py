@@ -50,10 +50,11 @@ def parse():
     ap.add_argument("--scale", type=int, default=None, help="R-MAT scale (default 20; 24 for --leg scale24)")
     ap.add_argument("--edges-log2", type=int, default=None, help="log2 of the edge count (default 24; 27)")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain / graphL / e2e / cpu legs")
-    ap.add_argument("--leg", default="bpp", choices=["bpp", "graphl", "batch", "scale24", "quality"],
+    ap.add_argument("--leg", default="bpp", choices=["bpp", "graphl", "batch", "scale24", "quality", "kruskal"],
                     help="bpp: the graphBpp line (default); graphl: graphL descent only; batch: uneven batch; "
                          "scale24: R-MAT 2^24 vertices / 2^27 edges, 4096 trees per step; "
-                         "quality: graphBpp min S and graphL min F against the planted state")
+                         "quality: graphBpp min S and graphL min F against the planted state; "
+                         "kruskal: graphBpp with randomized Kruskal trees instead of BFS trees")
     ap.add_argument("--R", type=int, default=256, help="graphL start points (--leg graphl)")
     ap.add_argument("--gl-steps", type=int, default=500, help="graphL descent steps (--leg graphl)")
     ap.add_argument("--graphs", type=int, default=4096, help="graphs in the uneven batch (--leg batch)")
@@ -241,6 +242,8 @@ def main():
         return scale_leg(args, P)
     if args.leg == "quality":
         return quality_leg(args, P)
+    if args.leg == "kruskal":
+        return kruskal_leg(args, P)
     n, u, v, s = workload(args)
     stream = torch.cuda.current_stream()
     sb = P.SignedBal(local, stream=stream)
@@ -696,6 +699,70 @@ def quality_leg(args, P, K_total=4096, R=256, steps=500, alpha=0.05):
             "planted_state_frustration": planted,
             "graphbpp_min_S_after_K_trees": mins, "graphbpp_distinct_states": int(cl["S"].shape[0]),
             "graphl_min_F_every_50_steps_then_final_by_start_points": gl}
+    print(json.dumps(line), flush=True)
+    sb.close()
+    return 0
+
+
+def kruskal_leg(args, P):
+    """graphBpp with the randomized Kruskal sampler on the 2^20 graph: K = 1024
+    trees per step (sample, count, hash, cloud), timed like the main line; the
+    BFS sampler's step on the same graph beside it, the smallest S and the
+    distinct states of both samplers over the same trees, and the oracle's
+    Kruskal trees on the host cores."""
+    import torch
+
+    n, u, v, s = workload(args)
+    stream = torch.cuda.current_stream()
+    sb = P.SignedBal(0, stream=stream)
+    n1, m1, _ = sb.load_graph(n, u, v, s)
+    K = TREES
+    steps_total = args.warmup + args.steps
+
+    def run(sample):
+        sb.cloud_reset(max_states=(steps_total + 2) * K + 64)
+        for i in range(args.warmup):
+            sample(SEED, i * K, K)
+            sb.frustration()
+            sb.cloud_insert()
+        torch.cuda.synchronize()
+        sb.profile_read()
+        sb.profile(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for i in range(args.steps):
+            sample(SEED, (args.warmup + i) * K, K)
+            sb.frustration()
+            sb.cloud_insert()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        sb.profile(False)
+        prof = sb.profile_read()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        cl, frmin = sb.cloud()
+        return {"ms_per_step": ms, "edge_evals_per_s": K * m1 / (ms / 1000.0),
+                "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
+                "gpu_launches_per_step": sum(c for _, c in prof.values()) / args.steps,
+                "fr_min": int(frmin), "distinct_states": int(cl["S"].shape[0]), "trees": steps_total * K}
+
+    kr = run(sb.sample_trees_kruskal)
+    bfs = run(sb.sample_trees)
+    line = {"leg": "kruskal", "metric": METRIC + " (Kruskal sampler)", "value": kr["edge_evals_per_s"], "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": kr["ms_per_step"],
+            "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+            "config": config_dict(args, n1, m1, 1), "kruskal": kr, "bfs_same_trees": bfs}
+    if not args.no_extras:
+        import oracle as O
+
+        g = oracle_graph(n, u, v, s)
+        cores = os.cpu_count() or 1
+        t = time.perf_counter()
+        with ThreadPoolExecutor(max_workers=cores) as ex:
+            list(ex.map(lambda i: O.mst_sample(g, SEED, 30_000_000 + i, 1, want_labels=False), range(cores)))
+        el = time.perf_counter() - t
+        line["cpu_baseline"] = {"value": cores * g.m / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{cores} Kruskal trees (sort, union-find, labels, count, hash), "
+                                          f"{cores} threads, {el:.1f} s"}
     print(json.dumps(line), flush=True)
     sb.close()
     return 0

@@ -211,6 +211,28 @@ sb_status sb_batch_cloud(sb_ctx* ctx, int32_t* n_states_out, int32_t* fr_min_out
  */
 sb_status sb_sample_trees(sb_ctx* ctx, uint64_t seed, int64_t tree_begin, int64_t K, int32_t* parents_out);
 
+/*
+ * Samples trees [tree_begin, tree_begin + K) with the randomized Kruskal
+ * sampler (appendix, tree samplers: Kruskal's algorithm on random edge
+ * weights drawn afresh for every tree) and their balanced states, in place of
+ * sb_sample_trees: sb_label, sb_frustration and sb_cloud then work on these
+ * trees the same way.  Tree t is the minimum spanning tree under the weights
+ *     w_t(u, v) = mix64(((u << 32) | v) ^ K_t)
+ * of the cleaned edges (u < v; ids local to each graph in a batch; K_t as in
+ * sb_sample_trees).  mix64 is a bijection, so the weights of one tree are
+ * distinct and the tree is unique (Prim's algorithm on the same weights finds
+ * it too).  The state labels each vertex with the parity of negative tree
+ * edges between it and vertex 0 (canonical: vertex 0 has label 0).  A tree is
+ * a pure function of (seed, t).  Works on a single graph and on a batch.
+ * K >= 1 (at most 64 * 64 per call).  in_tree_out (device, K x m bytes,
+ * nullable; edge order of sb_graph_edges): 1 where the edge is in the tree.
+ * Scratch: 36 bytes per (vertex, tree), at most 16 GiB per pass of trees.
+ * Errors: SB_ERR_ARG, SB_ERR_STATE (no graph), SB_ERR_OOM; a tree that does
+ * not span its graph (an internal error) is reported as SB_ERR_DEVICE_CHECK
+ * by the next sb_label / sb_frustration.  Replaces the previous batch.
+ */
+sb_status sb_sample_trees_kruskal(sb_ctx* ctx, uint64_t seed, int64_t tree_begin, int64_t K, uint8_t* in_tree_out);
+
 /* Canonical labels of the last batch, bit-packed vertex-major:
    labels_out[v * W + w] bit b = label of tree tree_begin + 64 w + b at vertex v,
    W = ceil(K / 64); bits of trees >= K are 0.  Host or device. */

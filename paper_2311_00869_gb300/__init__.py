@@ -172,6 +172,14 @@ class SignedBal:
         self._check(self.lib.sb_sample_trees(self.h, seed, tree_begin, K, _ptr(parents)))
         return parents
 
+    def sample_trees_kruskal(self, seed, tree_begin, K, want_in_tree=False):
+        """Randomized Kruskal trees [tree_begin, tree_begin + K) in place of
+        the BFS trees; with want_in_tree, a (K, m) uint8 membership matrix."""
+        in_tree = torch.empty((K, self.m), dtype=torch.uint8, device=self.device) if want_in_tree else None
+        self.K = K
+        self._check(self.lib.sb_sample_trees_kruskal(self.h, seed, tree_begin, K, _ptr(in_tree)))
+        return in_tree
+
     def label(self, out=None):
         """Canonical labels, (n, ceil(K/64)) int64 words (bit b of word w =
         tree 64w+b)."""

@@ -35,6 +35,7 @@ SIGNATURES = {
     "sb_graph_edges": (i32, [P, P, P, P]),
     "sb_graph_csr": (i32, [P, P, P, P]),
     "sb_sample_trees": (i32, [P, u64, i64, i64, P]),
+    "sb_sample_trees_kruskal": (i32, [P, u64, i64, i64, P]),
     "sb_label": (i32, [P, P]),
     "sb_frustration": (i32, [P, P, P]),
     "sb_cloud": (i32, [P, P, i64, ctypes.POINTER(i64), ctypes.POINTER(i32)]),

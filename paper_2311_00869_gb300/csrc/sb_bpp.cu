@@ -741,24 +741,15 @@ static sb_status check_sync_error(sb_ctx* c)
     SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
     if (err & 1u) return sb_fail(c, SB_ERR_TIMEOUT, "BFS grid barrier timed out");
     if (err & 2u) return sb_fail(c, SB_ERR_DEVICE_CHECK, "BFS exceeded n levels");
+    if (err & 4u) return sb_fail(c, SB_ERR_DEVICE_CHECK, "Kruskal trees did not span their graph");
     return SB_OK;
 }
 
-extern "C" sb_status sb_sample_trees(sb_ctx* c, uint64_t seed, int64_t tree_begin, int64_t K, int32_t* parents_out)
+sb_status sb_batch_begin(sb_ctx* c, uint64_t seed, int64_t tree_begin, int64_t K)
 {
-    if (!c) return SB_ERR_ARG;
-    if (!c->has_graph) return sb_fail(c, SB_ERR_STATE, "no graph loaded");
-    if (K < 1 || K > SB_TREES_MAX || tree_begin < 0)
-        return sb_fail(c, SB_ERR_ARG, "K must be in [1, %d] and tree_begin >= 0", SB_TREES_MAX);
-    if (parents_out && !sb_is_device_ptr(parents_out))
-        return sb_fail(c, SB_ERR_ARG, "parents_out must be a device pointer");
-    SB_CHECK_CUDA(c, cudaSetDevice(c->device));
     SB_TRY(ensure_sync(c));
     const int64_t n = c->n;
     const int W = (int)sb_cdiv(K, 64);
-    const int WL = c->tune[SB_TUNE_BFS_WORDS] > 0 ? (int)c->tune[SB_TUNE_BFS_WORDS] : SB_WORDS_MAX;  // words per launch
-    const int Wb_max = W < WL ? W : WL;
-    // batch storage
     size_t lab_bytes = sizeof(uint64_t) * (size_t)n * W;
     if (c->labels_cap < lab_bytes) {
         sb_dfree(c, c->labels);
@@ -772,6 +763,53 @@ extern "C" sb_status sb_sample_trees(sb_ctx* c, uint64_t seed, int64_t tree_begi
     c->flipw = (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * W * G);
     c->hashes = (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * 64 * W * G);
     c->counts = (int32_t*)sb_dalloc(c, sizeof(int32_t) * 64 * W * G);
+    c->has_batch = false;
+    if (!c->labels || !c->flipw || !c->hashes || !c->counts)
+        return sb_fail(c, SB_ERR_OOM, "batch storage (n=%lld, K=%lld)", (long long)n, (long long)K);
+    c->seed = seed;
+    c->tree_begin = tree_begin;
+    c->K = K;
+    c->W = W;
+    c->counts_valid = false;
+    c->batch_in_cloud = false;
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync + 16, 0, sizeof(uint32_t) * 16, c->stream));
+    return SB_OK;
+}
+
+sb_status sb_batch_end(sb_ctx* c)
+{
+    const int64_t n = c->n, G = c->batch_G > 0 ? c->batch_G : 1;
+    const int W = c->W;
+    k_flip<<<(unsigned)sb_cdiv((int64_t)W * G, 256), 256, 0, c->stream>>>(c->labels, W, c->flipw,
+                                                                          c->batch_G > 0 ? c->b_voff : nullptr, G);
+    SB_TRY(sb_after_launch(c, "k_flip"));
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->hashes, 0, sizeof(uint64_t) * 64 * W * G, c->stream));
+    {
+        SbProf prof(c, SB_PROF_HASH);
+        dim3 hg((unsigned)sb_cdiv(n, HASH_VCHUNK), (unsigned)W);
+        k_state_hash<<<hg, 256, 0, c->stream>>>(c->labels, n, W, c->flipw, c->vweight,
+                                                c->batch_G > 0 ? c->vgid : nullptr, 64 * (int64_t)W,
+                                                (unsigned long long*)c->hashes);
+        SB_TRY(sb_after_launch(c, "k_state_hash"));
+    }
+    c->has_batch = true;
+    return SB_OK;
+}
+
+extern "C" sb_status sb_sample_trees(sb_ctx* c, uint64_t seed, int64_t tree_begin, int64_t K, int32_t* parents_out)
+{
+    if (!c) return SB_ERR_ARG;
+    if (!c->has_graph) return sb_fail(c, SB_ERR_STATE, "no graph loaded");
+    if (K < 1 || K > SB_TREES_MAX || tree_begin < 0)
+        return sb_fail(c, SB_ERR_ARG, "K must be in [1, %d] and tree_begin >= 0", SB_TREES_MAX);
+    if (parents_out && !sb_is_device_ptr(parents_out))
+        return sb_fail(c, SB_ERR_ARG, "parents_out must be a device pointer");
+    SB_CHECK_CUDA(c, cudaSetDevice(c->device));
+    SB_TRY(sb_batch_begin(c, seed, tree_begin, K));
+    const int64_t n = c->n;
+    const int W = c->W;
+    const int WL = c->tune[SB_TUNE_BFS_WORDS] > 0 ? (int)c->tune[SB_TUNE_BFS_WORDS] : SB_WORDS_MAX;  // words per launch
+    const int Wb_max = W < WL ? W : WL;
     size_t words = (size_t)n * Wb_max;
     if (c->bfs_cap_words < words) {
         sb_dfree(c, c->vis);
@@ -788,36 +826,13 @@ extern "C" sb_status sb_sample_trees(sb_ctx* c, uint64_t seed, int64_t tree_begi
         c->bfs_cap_words = (c->vis && c->fr0 && c->fr1 && c->hubnew && c->hubbest) ? words : 0;
     }
     if (!c->done) c->done = (int32_t*)sb_dalloc(c, sizeof(int32_t) * (size_t)n);
-    if (!c->labels || !c->flipw || !c->hashes || !c->counts || !c->bfs_cap_words || !c->done) {
-        c->has_batch = false;
+    if (!c->bfs_cap_words || !c->done)
         return sb_fail(c, SB_ERR_OOM, "BFS batch storage (n=%lld, K=%lld)", (long long)n, (long long)K);
-    }
-    c->seed = seed;
-    c->tree_begin = tree_begin;
-    c->K = K;
-    c->W = W;
-    c->has_batch = false;
-    c->counts_valid = false;
-    c->batch_in_cloud = false;
-    SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync + 16, 0, sizeof(uint32_t) * 16, c->stream));
     for (int w0 = 0; w0 < W; w0 += WL) {
         int Wb = W - w0 < WL ? W - w0 : WL;
         SB_TRY(run_bfs(c, w0, Wb, parents_out));
     }
-    k_flip<<<(unsigned)sb_cdiv((int64_t)W * G, 256), 256, 0, c->stream>>>(c->labels, W, c->flipw,
-                                                                          c->batch_G > 0 ? c->b_voff : nullptr, G);
-    SB_TRY(sb_after_launch(c, "k_flip"));
-    SB_CHECK_CUDA(c, cudaMemsetAsync(c->hashes, 0, sizeof(uint64_t) * 64 * W * G, c->stream));
-    {
-        SbProf prof(c, SB_PROF_HASH);
-        dim3 hg((unsigned)sb_cdiv(n, HASH_VCHUNK), (unsigned)W);
-        k_state_hash<<<hg, 256, 0, c->stream>>>(c->labels, n, W, c->flipw, c->vweight,
-                                                c->batch_G > 0 ? c->vgid : nullptr, 64 * (int64_t)W,
-                                                (unsigned long long*)c->hashes);
-        SB_TRY(sb_after_launch(c, "k_state_hash"));
-    }
-    c->has_batch = true;
-    return SB_OK;
+    return sb_batch_end(c);
 }
 
 extern "C" sb_status sb_frustration(sb_ctx* c, int32_t* counts_out, uint64_t* hashes_out)

@@ -194,6 +194,14 @@ void sb_release_batch(sb_ctx* c)
     SB_FREE(done);
     SB_FREE(hubnew);
     SB_FREE(hubbest);
+    SB_FREE(mst_P);
+    SB_FREE(mst_R);
+    SB_FREE(mst_Y);
+    SB_FREE(mst_L);
+    SB_FREE(mst_B);
+    SB_FREE(mst_win);
+    SB_FREE(mst_flags);
+    c->mst_cap = 0;
     c->labels_cap = 0;
     c->bfs_cap_words = 0;
     c->has_batch = false;

@@ -138,6 +138,16 @@ struct sb_ctx {
     uint32_t* sync = nullptr;     // [0..2] level counters, [4] barrier count, [5] barrier gen, [6] error
     size_t bfs_cap_words = 0;
 
+    // Kruskal (Boruvka) scratch, [vertex][tree of the pass]
+    uint32_t* mst_P = nullptr;    // parent << 1 | parity to it
+    uint32_t* mst_R = nullptr;    // root << 1 | parity to it, at the start of a round
+    uint32_t* mst_Y = nullptr;    // lightest outgoing neighbour | neg << 31, or SB_MST_DEAD
+    uint64_t* mst_L = nullptr;    // its weight
+    uint64_t* mst_B = nullptr;    // lightest outgoing weight of the component this vertex roots
+    int2* mst_win = nullptr;      // (inside endpoint, outside endpoint | neg << 31) of that edge, or -1
+    int32_t* mst_flags = nullptr; // [r] = 1 when round r - 1 merged something
+    size_t mst_cap = 0;           // (vertex, tree) slots held
+
     // cloud
     int64_t cl_max = 0;
     int64_t cl_slots = 0;
@@ -235,6 +245,11 @@ sb_status sb_radix_sort_u64(sb_ctx* c, uint64_t* keys, int64_t n, int bits);
 sb_status sb_cloud_insert_batch(sb_ctx* c);
 sb_status sb_cloud_alloc(sb_ctx* c);
 sb_status sb_score_batch(sb_ctx* c);
+// sampled-batch storage for trees [tree_begin, tree_begin + K) (labels,
+// canonical flips, counts, hashes), then the canonical flip and state hash
+// once a sampler has written raw labels
+sb_status sb_batch_begin(sb_ctx* c, uint64_t seed, int64_t tree_begin, int64_t K);
+sb_status sb_batch_end(sb_ctx* c);
 
 #define SB_CHECK_CUDA(ctx, call)                                   \
     do {                                                           \

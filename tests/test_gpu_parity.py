@@ -394,6 +394,27 @@ def test_rmat_2pow20_sampled_trees(P, sb, rmat20):
     assert np.all(counts >= 0) and np.all(counts <= g.m - g.n + 1)
 
 
+def test_rmat_2pow20_kruskal_sampled_trees(P, sb, rmat20):
+    """Randomized Kruskal trees on the 2^20-vertex graph, 1024 in one call
+    (two passes of trees): trees 5 and 1000, one per pass, against the oracle
+    bit for bit."""
+    (n, u, v, s), g = rmat20
+    sb.load_graph(n, u, v, s)
+    K = 1024
+    sb.sample_trees_kruskal(2, 0, K)
+    counts, hashes = sb.frustration()
+    counts, hashes = counts.cpu().numpy(), hashes.cpu().numpy().view(np.uint64)
+    labw = sb.label().cpu().numpy().view(np.uint64)
+    for t in (5, 1000):
+        k, _, clab = O.mst_tree(g, 2, t)
+        assert k == g.n - 1
+        assert counts[t] == O.frustration(g, clab)
+        assert hashes[t] == np.uint64(O.state_hash(clab))
+        lab = ((labw[:, t // 64] >> np.uint64(t % 64)) & np.uint64(1)).astype(np.uint8)
+        assert np.array_equal(lab, clab)
+    assert np.all(counts >= 0) and np.all(counts <= g.m - g.n + 1)
+
+
 def test_graphl_gradient_central_differences_2000_vertex_subgraph(P, sb, rmat20):
     """The adjoint on a 2,000-vertex piece of the benchmark graph (the first
     2,000 vertices a BFS from vertex 0 reaches, their induced subgraph, its
