@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(MST_THREADS) k_mst_init(MstArgs A)
     }
 }
 
-// 1. lightest edge leaving the component, per (vertex, tree); component min
+// 1. lightest edge leaving the component, per (vertex, tree); component min.
+// In round 0 every vertex is alone, so every edge leaves and nothing is loaded.
 __global__ void __launch_bounds__(MST_THREADS) k_mst_min(MstArgs A, int r)
 {
     if (!A.flags[r]) return;
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(MST_THREADS) k_mst_min(MstArgs A, int r)
         for (int32_t p = A.rowptr[v]; p < e1; p++) {
             const uint32_t cv = (uint32_t)A.col[p];
             const uint32_t y = cv & SB_ID_MASK;
-            if ((A.R[(int64_t)y * A.T + tt] >> 1) == c) continue;
+            if (r > 0 && (A.R[(int64_t)y * A.T + tt] >> 1) == c) continue;
             const uint32_t yl = (uint32_t)(y - base);
             const uint64_t pair = vl < yl ? ((uint64_t)vl << 32 | yl) : ((uint64_t)yl << 32 | vl);
             const uint64_t w = sb_mix64(pair ^ kt);
