@@ -123,7 +123,8 @@ sb_status sb_get_tuning(sb_ctx* ctx, int32_t knob, int64_t* value);
    launches, [2] neighbour entries scanned (per vertex-word lane),
    [3] hashed parent candidates of whole rows, [4] always 0 (kept so that
    the layout stays; every row is scanned in one pass), [5] hashed parent
-   candidates of split rows.  Synchronises the stream. */
+   candidates of split rows.  All zero after sb_sample_trees_kruskal.
+   Synchronises the stream. */
 #define SB_STATS_N 6
 sb_status sb_stats(sb_ctx* ctx, int64_t* out, int32_t n);
 
