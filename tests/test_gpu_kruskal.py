@@ -110,3 +110,28 @@ def test_kruskal_batch_matches_per_graph_oracle(P):
             assert np.array_equal(it[:, eoff[gi]:eoff[gi + 1]], ref["in_tree"]), gi
     finally:
         sb.close()
+
+
+def test_kruskal_argument_and_state_errors(P):
+    """Out-of-order calls and out-of-range arguments come back as status
+    codes; the largest K of one call is still exact."""
+    ARG, STATE = -1, -10
+    sb = P.SignedBal(0)
+    try:
+        with pytest.raises(P.SignedBalError) as e:
+            sb.sample_trees_kruskal(0, 0, 8)
+        assert e.value.code == STATE
+        n, u, v, s = synth.random_connected(50, 80, seed=6)
+        g = O.clean_graph(n, u, v, s)
+        sb.load_graph(n, u, v, s)
+        for K, t0 in ((0, 0), (4097, 0), (8, -1)):
+            with pytest.raises(P.SignedBalError) as e:
+                sb.sample_trees_kruskal(0, t0, K)
+            assert e.value.code == ARG
+        host = np.zeros((8, g.m), np.uint8)  # in_tree must be device memory
+        with pytest.raises(P.SignedBalError) as e:
+            sb._check(sb.lib.sb_sample_trees_kruskal(sb.h, 0, 0, 8, host.ctypes.data))
+        assert e.value.code == ARG
+        _check(P, sb, g, seed=1, t0=0, K=4096)
+    finally:
+        sb.close()
