@@ -301,6 +301,35 @@ def test_kruskal_trees_are_minimum_spanning_trees(oracle, case):
         assert res["hashes"][t] == np.uint64(oracle.state_hash(clab))
 
 
+def test_kruskal_tree_equals_prims_tree(oracle):
+    """Prim's algorithm (the appendix's other weighted sampler) grown from
+    vertex 0 on the same weights gives the same tree: with distinct weights
+    the minimum spanning tree is unique."""
+    import heapq
+
+    n, u, v, s = synth.random_connected(30, 60, seed=808)
+    g = oracle.clean_graph(n, u, v, s)
+    adj = [[] for _ in range(g.n)]
+    for e, (a, b) in enumerate(zip(g.eu.tolist(), g.ev.tolist())):
+        adj[a].append((b, e))
+        adj[b].append((a, e))
+    for t in range(8):
+        w = [oracle.mst_weight(3, t, a, b) for a, b in zip(g.eu.tolist(), g.ev.tolist())]
+        inside, heap, tree = {0}, [(w[e], e, y) for y, e in adj[0]], set()
+        heapq.heapify(heap)
+        while heap:
+            _, e, y = heapq.heappop(heap)
+            if y in inside:
+                continue
+            inside.add(y)
+            tree.add(e)
+            for z, f in adj[y]:
+                if z not in inside:
+                    heapq.heappush(heap, (w[f], f, z))
+        _, in_tree, _ = oracle.mst_tree(g, 3, t)
+        assert set(np.nonzero(in_tree)[0].tolist()) == tree
+
+
 def test_kruskal_harary_planted_balance(oracle):
     n, u, v, s, side = synth.planted_balanced(16, 20, seed=601)
     g = oracle.clean_graph(n, u, v, s)

@@ -1,6 +1,7 @@
 """Multi-rank graphBpp on the host: tree ranges per rank and the merge of the
 per-rank frustration clouds, run as world-size-2 gloo process groups on CPU
-with the oracle standing in for each rank's device work."""
+with the oracle standing in for each rank's device work (BFS trees and
+Kruskal trees shard the same way: both are pure functions of the tree index)."""
 import os
 import socket
 import tempfile
@@ -20,15 +21,21 @@ def _graph(O):
     return O.clean_graph(n, u, v, s)
 
 
-def _part(O, g, t0, count):
-    smp = O.sample(g, SEED, t0, count)
+def _sample(O, g, t0, count, sampler):
+    if sampler == "kruskal":
+        return O.mst_sample(g, SEED, t0, count)
+    return O.sample(g, SEED, t0, count)
+
+
+def _part(O, g, t0, count, sampler):
+    smp = _sample(O, g, t0, count, sampler)
     cl = O.cloud(smp["labels"], smp["counts"], t0=t0)
     first = cl["first_tree"]
     labels = [np.packbits(smp["labels"][int(f) - t0]) for f in first]
     return {"hash": cl["H"], "S": cl["S"], "count": cl["count"], "first_tree": first, "labels": labels}
 
 
-def _rank_main(rank, world, port, out_path, with_labels):
+def _rank_main(rank, world, port, out_path, with_labels, sampler):
     import torch.distributed as dist
 
     import oracle as O
@@ -40,7 +47,7 @@ def _rank_main(rank, world, port, out_path, with_labels):
         parts = []
         for step in range(STEPS):
             t0, cnt = shard.tree_range(rank, world, step, K)
-            parts.append(_part(O, g, t0, cnt))
+            parts.append(_part(O, g, t0, cnt, sampler))
         local = shard.merge_clouds(parts)
         if not with_labels:
             local.pop("labels")
@@ -58,17 +65,17 @@ def _free_port():
         return s.getsockname()[1]
 
 
-@pytest.mark.parametrize("with_labels", [True, False])
-def test_two_rank_cloud_equals_single_process(oracle, with_labels):
+@pytest.mark.parametrize("with_labels,sampler", [(True, "bfs"), (False, "bfs"), (True, "kruskal")])
+def test_two_rank_cloud_equals_single_process(oracle, with_labels, sampler):
     world = 2
     with tempfile.TemporaryDirectory() as d:
         out = os.path.join(d, "merged.npz")
-        mp.start_processes(_rank_main, args=(world, _free_port(), out, with_labels), nprocs=world, join=True,
-                           start_method="spawn")
+        mp.start_processes(_rank_main, args=(world, _free_port(), out, with_labels, sampler), nprocs=world,
+                           join=True, start_method="spawn")
         got = dict(np.load(out))
     g = _graph(oracle)
     total = STEPS * world * K
-    smp = oracle.sample(g, SEED, 0, total)
+    smp = _sample(oracle, g, 0, total, sampler)
     ref = oracle.cloud(smp["labels"], smp["counts"], t0=0)
     assert len(ref["H"]) > 3  # several distinct states, so the merge is exercised
     np.testing.assert_array_equal(got["hash"], ref["H"])
