@@ -228,7 +228,9 @@ sb_status sb_sample_trees(sb_ctx* ctx, uint64_t seed, int64_t tree_begin, int64_
  * K >= 1 (at most 64 * 64 per call).  in_tree_out (device, K x m bytes,
  * nullable; edge order of sb_graph_edges): 1 where the edge is in the tree.
  * Scratch: 36 bytes per (vertex, tree); a pass of trees takes at most
- * 16 GiB and half the free device memory (at least 64 trees per pass).
+ * 16 GiB and half the free device memory (at least 64 trees per pass).  The
+ * context keeps it for the next call until a graph is loaded or the context
+ * is destroyed.
  * Errors: SB_ERR_ARG, SB_ERR_STATE (no graph), SB_ERR_OOM; a tree that does
  * not span its graph (an internal error) is reported as SB_ERR_DEVICE_CHECK
  * by the next sb_label / sb_frustration.  Replaces the previous batch.
