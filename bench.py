@@ -90,7 +90,7 @@ def config_dict(args, n_clean, m_clean, world):
         "trees_per_step": TREES,
         "words_per_launch": TREES // 64,
         "l2": "inputs larger than L2 (CSR 2m x 4 B plus labels and BFS state exceed 129 MB)",
-        "parallelism": f"replicas{world}" if world > 1 else "single-gpu",
+        "parallelism": f"tree ranges sharded over {world} ranks" if world > 1 else "single-gpu",
     }
 
 
