@@ -330,6 +330,39 @@ def test_kruskal_tree_equals_prims_tree(oracle):
         assert set(np.nonzero(in_tree)[0].tolist()) == tree
 
 
+def test_kruskal_tree_distribution_on_k4_matches_random_edge_orders(oracle):
+    """On the complete graph K4 the hashed weights must act like a uniformly
+    random edge order: the frequency of each of the 16 spanning trees over
+    20,000 trees matches the exact law of Kruskal's algorithm over all 720
+    edge orders (brute force), within 4 standard deviations."""
+    import itertools
+
+    eu = [0, 0, 0, 1, 1, 2]
+    ev = [1, 2, 3, 2, 3, 3]
+    g = oracle.clean_graph(4, eu, ev, [1] * 6)
+    exact = {}
+    for order in itertools.permutations(range(6)):
+        comp, tree = list(range(4)), []
+        for e in order:
+            a, b = comp[g.eu[e]], comp[g.ev[e]]
+            if a != b:
+                comp = [a if c == b else c for c in comp]
+                tree.append(e)
+        key = tuple(sorted(tree))
+        exact[key] = exact.get(key, 0) + 1
+    assert len(exact) == 16 and sum(exact.values()) == 720
+    K = 20000
+    got = oracle.mst_sample(g, seed=21, t0=0, K=K, want_labels=False, want_in_tree=True)["in_tree"]
+    seen = {}
+    for row in got:
+        key = tuple(np.nonzero(row)[0].tolist())
+        seen[key] = seen.get(key, 0) + 1
+    assert set(seen) == set(exact)
+    for key, cnt in exact.items():
+        p = cnt / 720
+        assert abs(seen[key] - K * p) <= 4 * np.sqrt(K * p * (1 - p)), (key, seen[key], K * p)
+
+
 def test_kruskal_harary_planted_balance(oracle):
     n, u, v, s, side = synth.planted_balanced(16, 20, seed=601)
     g = oracle.clean_graph(n, u, v, s)
