@@ -49,6 +49,46 @@ def test_hash_primitives_are_bijective_on_samples(oracle):
     assert oracle.fmix32(0) == 0
 
 
+def _murmur3_x86_32(data: bytes, seed: int, fmix) -> int:
+    """MurmurHash3_x86_32 (Appleby, SMHasher): 4-byte little-endian blocks
+    mixed with c1 = 0xcc9e2d51, c2 = 0x1b873593 and rotations by 15 and 13,
+    the tail bytes, the length, then the 32-bit finaliser `fmix` under test."""
+    M = 0xFFFFFFFF
+    rotl = lambda x, r: ((x << r) | (x >> (32 - r))) & M
+    c1, c2 = 0xCC9E2D51, 0x1B873593
+    h = seed & M
+    nb = len(data) // 4
+    for i in range(nb):
+        k = int.from_bytes(data[4 * i:4 * i + 4], "little")
+        k = rotl((k * c1) & M, 15)
+        h ^= (k * c2) & M
+        h = (rotl(h, 13) * 5 + 0xE6546B64) & M
+    tail = data[4 * nb:]
+    if tail:
+        k = int.from_bytes(tail, "little")
+        k = rotl((k * c1) & M, 15)
+        h ^= (k * c2) & M
+    h ^= len(data)
+    return fmix(h)
+
+
+@pytest.mark.parametrize("data,seed,want", [
+    (b"", 0, 0x00000000),
+    (b"", 1, 0x514E28B7),  # = fmix32(1)
+    (b"", 0xFFFFFFFF, 0x81F16F39),  # = fmix32(0xFFFFFFFF)
+    (b"\0\0\0\0", 0, 0x2362F9DE),
+    (b"aaaa", 0x9747B28C, 0x5A97808A),
+    (b"abc", 0, 0xB3DD93FA),
+    (b"Hello, world!", 0x9747B28C, 0x24884CBA),
+    (b"The quick brown fox jumps over the lazy dog", 0x9747B28C, 0x2FA826CD),
+])
+def test_fmix32_gives_published_murmur3_vectors(oracle, data, seed, want):
+    # The MurmurHash3 finaliser is the last step of MurmurHash3_x86_32; the
+    # empty key reduces the whole hash to fmix32(seed).  Published test
+    # vectors of the full hash therefore pin every constant and shift of it.
+    assert _murmur3_x86_32(data, seed, oracle.fmix32) == want
+
+
 def test_state_hash_is_a_subset_sum(oracle):
     rng = np.random.Generator(np.random.PCG64(9))
     n = 300
@@ -479,6 +519,36 @@ def test_scalable_cloud_with_eviction_invariants(oracle, fmax):
     assert len(b["S"]) == fmax  # the case fills the cloud, so eviction happened
 
 
+def test_scalable_cloud_evicts_the_lowest_slot_of_largest_S(oracle):
+    """A hand-built tree sequence for the scalable cloud (appendix algorithm
+    alg-scale, R14 reading) with fmax = 3, where the largest stored S is held
+    by two slots twice.  Walking the rule by hand (slot contents after each
+    tree):
+      t0 A9 -> [A9]          t1 B7 -> [A9 B7]        t2 C7 -> [A9 B7 C7]
+      t3 D6 -> [D6 B7 C7]    (replaces the one largest, A9)
+      t4 E5 -> [D6 E5 C7]    (B7 and C7 tie: the lower slot, B, goes)
+      t5 F4 -> [D6 E5 F4]    t6 G4 -> [G4 E5 F4]     t7 H3 -> [G4 H3 F4]
+      t8 I2 -> [I2 H3 F4]    (G4 and F4 tie: the lower slot, G, goes)
+      t9 F4 -> not below the largest S (4): not counted
+      t10 H3 -> below 4 and stored: H counted twice
+    Output by storing tree: F (t5), H (t7), I (t8).  Evicting the higher slot
+    among equals would end with G (t6), H (t7), I (t8) instead."""
+    n = 6
+    states = {}
+    for name in "ABCDEFGHI":  # distinct canonical labellings (vertex 0 on the +1 side)
+        i = "ABCDEFGHI".index(name) + 1
+        states[name] = np.array([0] + [(i >> b) & 1 for b in range(n - 1)], np.uint8)
+    seq = [("A", 9), ("B", 7), ("C", 7), ("D", 6), ("E", 5), ("F", 4), ("G", 4), ("H", 3), ("I", 2),
+           ("F", 4), ("H", 3)]
+    labels = np.stack([states[a] for a, _ in seq])
+    counts = np.array([c for _, c in seq], np.int32)
+    b = oracle.cloud_bounded(labels, counts, fmax=3, t0=100)
+    assert b["first_tree"].tolist() == [105, 107, 108]
+    assert b["S"].tolist() == [4, 3, 2]
+    assert b["count"].tolist() == [1, 2, 1]
+    assert [int(h) for h in b["H"]] == [oracle.state_hash(states[x]) for x in "FHI"]
+
+
 def test_graphl_gradient_central_differences(oracle):
     g = _small_graph(oracle)
     R = 3
@@ -530,6 +600,73 @@ def test_graphl_descent_is_a_matrix_power(oracle):
     want = np.linalg.matrix_power(np.eye(g.n) + 0.5 * alpha * A, steps) @ gam0
     assert np.allclose(out, want, rtol=1e-10, atol=1e-12)
     assert np.all(exps == 0)
+
+
+def _signed_adjacency(g):
+    A = np.zeros((g.n, g.n))
+    for a, b, s in zip(g.eu, g.ev, g.eneg):
+        A[a, b] = A[b, a] = -1.0 if s else 1.0
+    return A
+
+
+U32 = 2.0**-24  # unit roundoff of float32
+
+
+def test_graphl_grad_f32_within_its_rounding_bound(oracle):
+    """Eq. 4 in float32: each component is a sequential sum of deg(v) terms
+    times -1/2 and the upstream weight, so it lies within
+    (deg(v) + 1) u * 1/2 |gout| sum_j |G_j| of the float64 gradient (standard
+    bound of recursive summation, u = 2^-24).  The float64 gradient is pinned
+    by central differences above; here it is also recomputed as
+    -1/2 A_sigma G with numpy."""
+    g = _small_graph(oracle, seed=11)
+    R = 5
+    gam = synth.gamma0(g.n, R, seed=12)
+    gout = np.array([1.0, -2.0, 0.5, 3.0, 0.25], np.float32)
+    A = _signed_adjacency(g)
+    g64 = oracle.graphl_grad_f64(g, gam.astype(np.float64), gout.astype(np.float64))
+    assert np.allclose(g64, -0.5 * (A @ gam.astype(np.float64)) * gout[None, :], rtol=1e-12, atol=1e-14)
+    g32 = oracle.graphl_grad_f32(g, gam, gout)
+    deg = np.abs(A).sum(axis=1)
+    bound = (deg[:, None] + 1) * U32 * 0.5 * np.abs(gout)[None, :] * (np.abs(A) @ np.abs(gam.astype(np.float64)))
+    assert np.all(np.abs(g32.astype(np.float64) - g64) <= bound * 1.0001 + 1e-30)
+    # the norm-wise contract of the float32 path
+    assert np.linalg.norm(g32 - g64) <= 1e-5 * np.linalg.norm(g64)
+    # sign: with every edge positive and G > 0 the gradient is negative (Eq. 4)
+    pos = oracle.Graph(g.n, g.eu, g.ev, np.zeros(g.m, np.int8))
+    gp = oracle.graphl_grad_f32(pos, np.abs(gam) + 0.5)
+    assert np.all(gp < 0)
+
+
+def test_graphl_descent_f32_follows_the_matrix_power_within_its_bound(oracle):
+    """Alg. 2 in float32: lambda updates G <- G - alpha dL/dG are lambda
+    products with B = I + alpha/2 A_sigma.  Each float32 update adds an error
+    of at most (deg + 3) u (|B| |G|) per component, so after lambda steps
+    |G32 - B^lambda G0| <= lambda (dmax + 3) u |B|^lambda |G0| to first
+    order (a 1 % margin covers the second-order terms)."""
+    g = _small_graph(oracle, seed=13)
+    A = _signed_adjacency(g)
+    alpha, steps = 0.05, 40
+    gam0 = synth.gamma0(g.n, 4, seed=14)
+    out, exps = oracle.graphl_descent_f32(g, gam0, alpha, steps, renorm_log2=0)
+    assert np.all(exps == 0)
+    B = np.eye(g.n) + 0.5 * alpha * A
+    want = np.linalg.matrix_power(B, steps) @ gam0.astype(np.float64)
+    dmax = np.abs(A).sum(axis=1).max()
+    bound = steps * (dmax + 3) * U32 * (np.linalg.matrix_power(np.abs(B), steps) @ np.abs(gam0.astype(np.float64)))
+    err = np.abs(out.astype(np.float64) - want)
+    assert np.all(err <= 1.01 * bound)
+    # the bound is tight enough to catch a sign error in the update
+    wrong = np.linalg.matrix_power(np.eye(g.n) - 0.5 * alpha * A, steps) @ gam0.astype(np.float64)
+    assert np.any(np.abs(out.astype(np.float64) - wrong) > 1.01 * bound)
+    # with renormalisation: signs and values up to the recorded power of two
+    out2, exps2 = oracle.graphl_descent_f32(g, gam0, 0.9, 30, renorm_log2=4)
+    ref2 = np.linalg.matrix_power(np.eye(g.n) + 0.45 * A, 30) @ gam0.astype(np.float64)
+    assert np.all(exps2 > 0)
+    scaled = out2.astype(np.float64) * np.exp2(exps2.astype(np.float64))[None, :]
+    big = np.abs(ref2) > 1e-3 * np.abs(ref2).max(axis=0, keepdims=True)
+    assert np.array_equal(np.sign(scaled[big]), np.sign(ref2[big]))
+    assert np.allclose(scaled, ref2, rtol=1e-4, atol=1e-4 * np.abs(ref2).max())
 
 
 def test_graphl_renorm_keeps_signs(oracle):
