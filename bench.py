@@ -1,19 +1,24 @@
 #!/usr/bin/env python3
 """graphBpp / graphL benchmark on GB300 (one JSON line on rank 0).
 
-Workload (N=1): the 2^20-vertex R-MAT signed graph (a,b,c,d = 0.57, 0.19,
-0.19, 0.05; 2^24 distinct undirected edges; planted two-faction balance with
-10% iid sign flips; largest connected component), K = 1024 randomized-BFS
-trees per step in one batched launch (16 words of 64 trees).  One step is the
-whole graphBpp hot path on one batch: tree sampling + parity labels + state
-hash (sb_sample_trees), frustration counts (sb_frustration) and cloud
-insertion (sb_cloud).  Ingest is done once, outside the timed region (it is
-timed inside the e2e leg).  Metric: edge-evals/s = trees x |E| / s.
+Workload (N=1): the paper-scale R-MAT signed graph with 2^24 vertex ids and
+2^27 distinct undirected edges (a,b,c,d = 0.57, 0.19, 0.19, 0.05; three
+planted factions 94.8 / 2.6 / 2.6 %, inter-faction edges negative, 15 % iid
+sign flips; largest connected component), K = 4096 randomized-BFS trees per
+step (64 words of 64 trees).  One step is the whole graphBpp hot path on one
+batch: tree sampling + parity labels + state hash (sb_sample_trees),
+frustration counts (sb_frustration) and cloud insertion (sb_cloud).  Ingest is
+done once, outside the timed region (it is timed inside the e2e leg).
+Metric: edge-evals/s = trees x |E| / s.  The inputs (CSR 1.07 GB, labels
+3.8 GB) are far larger than L2, so no flush is needed between steps.
 
-Also reported: the plain path (one tree per launch) on the same GPU, graphL
-steps/s (R = 256 start points on the same graph), the end-to-end number
-through the C ABI with host buffers, the roofline of the dominant kernel and
-the CPU oracle on the host cores.
+Also reported: the 2^20-vertex workload (1024 trees per step), the plain path
+(one tree per launch) against one batched launch at the same cloud on the
+1,000-vertex Erdos-Renyi graph and on the 2^20 graph, graphL steps/s (R = 256
+start points, 500 steps, against one start point per launch at the same F),
+the end-to-end number through the C ABI with host buffers, the roofline of
+the dominant kernel against a measured ceiling and the CPU oracle on the host
+cores.
 
 --impl reference times the CPU oracle (plain C, all host cores through a
 thread pool) on the same workload and metric.
@@ -36,9 +41,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "graphBpp edge-evals/s (trees x |E| / s), batched"
 UNIT = "edge-evals/s"
-WORKLOAD = "rmat20_2faction_K1024"
-TREES = 1024
 SEED = 0
+# name -> (R-MAT scale, log2 of the edges, planted factions, trees per step)
+WORKLOADS = {
+    "rmat24": (24, 27, 3, 4096),
+    "rmat20": (20, 24, 2, 1024),
+}
+WORKLOAD_NAMES = {"rmat24": "rmat24_3faction_K4096", "rmat20": "rmat20_2faction_K1024"}
 
 
 def parse():
@@ -47,12 +56,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--scale", type=int, default=None, help="R-MAT scale (default 20; 24 for --leg scale24)")
-    ap.add_argument("--edges-log2", type=int, default=None, help="log2 of the edge count (default 24; 27)")
-    ap.add_argument("--no-extras", action="store_true", help="skip the plain / graphL / e2e / cpu legs")
-    ap.add_argument("--leg", default="bpp", choices=["bpp", "graphl", "batch", "scale24", "quality", "kruskal"],
+    ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS),
+                    help="rmat24: 2^24 vertex ids, 2^27 edges, three factions, 4096 trees per step (default); "
+                         "rmat20: 2^20 vertex ids, 2^24 edges, two factions, 1024 trees per step")
+    ap.add_argument("--scale", type=int, default=None, help="R-MAT scale (overrides the workload's)")
+    ap.add_argument("--edges-log2", type=int, default=None, help="log2 of the edge count (overrides the workload's)")
+    ap.add_argument("--trees", type=int, default=None, help="trees per step (overrides the workload's)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the side legs, e2e and the CPU baseline")
+    ap.add_argument("--leg", default="bpp", choices=["bpp", "graphl", "batch", "quality", "kruskal"],
                     help="bpp: the graphBpp line (default); graphl: graphL descent only; batch: uneven batch; "
-                         "scale24: R-MAT 2^24 vertices / 2^27 edges, 4096 trees per step; "
                          "quality: graphBpp min S and graphL min F against the planted state; "
                          "kruskal: graphBpp with randomized Kruskal trees instead of BFS trees")
     ap.add_argument("--R", type=int, default=256, help="graphL start points (--leg graphl)")
@@ -61,9 +73,14 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="keep the default tuning knobs")
     ap.add_argument("--gl-lanes", type=int, default=0, help="graphL lanes per row segment (8 or 32; with --no-tune)")
     args = ap.parse_args()
-    big = args.leg == "scale24"
-    args.scale = args.scale if args.scale is not None else (24 if big else 20)
-    args.edges_log2 = args.edges_log2 if args.edges_log2 is not None else (27 if big else 24)
+    if args.leg in ("graphl", "quality", "kruskal") and args.workload == "rmat24" and args.scale is None:
+        args.workload = "rmat20"  # these legs run on the 2^20 two-faction graph
+    sc, el, fac, K = WORKLOADS[args.workload]
+    args.custom = args.scale is not None or args.edges_log2 is not None
+    args.scale = args.scale if args.scale is not None else sc
+    args.edges_log2 = args.edges_log2 if args.edges_log2 is not None else el
+    args.factions = fac
+    args.K = args.trees if args.trees is not None else K
     return args
 
 
@@ -74,21 +91,36 @@ def dist_env():
     return rank, world, local
 
 
-def workload(args):
+def gen_graph(scale, edges_log2, factions, workers=0):
+    """(n, src, dst, sign) of the R-MAT workload (drawn before any CUDA call:
+    the three-faction draw may use a spawned process pool)."""
     import synth
 
-    n, u, v, s = synth.rmat_two_faction(scale=args.scale, m_target=1 << args.edges_log2)
-    return n, u, v, s
+    if factions == 3:
+        return synth.rmat_three_faction(scale=scale, m_target=1 << edges_log2, workers=workers)
+    return synth.rmat_two_faction(scale=scale, m_target=1 << edges_log2)
+
+
+def workload_name(args):
+    if args.custom:
+        return f"rmat{args.scale}_e{args.edges_log2}"
+    return WORKLOAD_NAMES[args.workload]
+
+
+def graph_text(scale, edges_log2, factions):
+    noise = "three factions (94.8 / 2.6 / 2.6 %, inter-faction negative) + 15% sign noise" if factions == 3 \
+        else "two factions + 10% sign noise"
+    return f"R-MAT scale {scale}, 2^{edges_log2} undirected edges, {noise}, LCC"
 
 
 def config_dict(args, n_clean, m_clean, world):
     return {
-        "workload": WORKLOAD if (args.scale, args.edges_log2) == (20, 24) else f"rmat{args.scale}_e{args.edges_log2}",
-        "graph": f"R-MAT scale {args.scale}, 2^{args.edges_log2} undirected edges, two factions + 10% sign noise, LCC",
+        "workload": workload_name(args),
+        "graph": graph_text(args.scale, args.edges_log2, args.factions),
         "n": n_clean,
         "m": m_clean,
-        "trees_per_step": TREES,
-        "words_per_launch": TREES // 64,
+        "trees_per_step": args.K,
+        "words_per_step": (args.K + 63) // 64,
         "l2": "inputs larger than L2 (CSR 2m x 4 B plus labels and BFS state exceed 129 MB)",
         "parallelism": f"tree ranges sharded over {world} ranks" if world > 1 else "single-gpu",
     }
@@ -154,37 +186,45 @@ def oracle_graph(n, u, v, s):
     return O.clean_graph(n, u, v, s)
 
 
-def oracle_trees(g, t0, count, cores):
-    """Samples `count` trees with the oracle on `cores` threads; returns seconds."""
+def oracle_trees(g, t0, count, cores, want=False):
+    """Samples trees [t0, t0 + count) with the oracle, one tree per task on
+    `cores` threads; returns (seconds, per-tree results if want)."""
     import oracle as O
 
     t = time.perf_counter()
     with ThreadPoolExecutor(max_workers=cores) as ex:
-        list(ex.map(lambda i: O.sample(g, SEED, t0 + i, 1, want_labels=False), range(count)))
-    return time.perf_counter() - t
+        res = list(ex.map(lambda i: O.sample(g, SEED, t0 + i, 1, want_labels=False), range(count)))
+    return time.perf_counter() - t, (res if want else None)
 
 
-def cpu_baseline(g, budget_s=12.0, single_budget_s=3.0):
+def cpu_baseline(sb, g, t0=10_000_000, budget_s=10.0):
+    """The oracle on the host cores: rounds of one tree per core (BFS tree,
+    labels, count, hash) until `budget_s` has passed; the trees of the first
+    round are also checked bit for bit against the GPU's."""
     cores = os.cpu_count() or 1
-    done, el = 0, 0.0
+    done, el, first = 0, 0.0, None
     while el < budget_s:
-        el += oracle_trees(g, 10_000_000 + done, cores, cores)
+        dt, res = oracle_trees(g, t0 + done, cores, cores, want=first is None)
+        if first is None:
+            first = res
+        el += dt
         done += cores
-    one, el1 = 0, 0.0
-    while el1 < single_budget_s:
-        el1 += oracle_trees(g, 20_000_000 + one, 1, 1)
-        one += 1
+    sb.sample_trees(SEED, t0, cores)
+    counts, hashes = sb.frustration()
+    counts, hashes = counts.cpu().numpy(), hashes.cpu().numpy().view(np.uint64)
+    same = all(int(counts[i]) == int(r["counts"][0]) and int(hashes[i]) == int(r["hashes"][0])
+               for i, r in enumerate(first))
     return {"value": done * g.m / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{done} trees (BFS tree, labels, count, hash) of the same graph, {cores} threads, {el:.1f} s",
-            "single_thread": {"value": one * g.m / el1, "unit": UNIT, "cores": 1,
-                              "sample": f"{one} trees on one thread, {el1:.1f} s"}}
+            "sample": f"{done} trees (BFS tree, labels, count, hash) of the same graph, one per thread on "
+                      f"{cores} threads, {el:.1f} s",
+            "bit_exact_on_first_round": bool(same)}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    n, u, v, s = workload(args)
+    n, u, v, s = gen_graph(args.scale, args.edges_log2, args.factions, workers=os.cpu_count() or 1)
     g = oracle_graph(n, u, v, s)
     cores = os.cpu_count() or 1
     per_step = cores
@@ -192,7 +232,7 @@ def run_reference(args):
         oracle_trees(g, i * per_step, per_step, cores)
     el = 0.0
     for i in range(args.steps):
-        el += oracle_trees(g, (args.warmup + i) * per_step, per_step, cores)
+        el += oracle_trees(g, (args.warmup + i) * per_step, per_step, cores)[0]
     value = args.steps * per_step * g.m / el
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -200,7 +240,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": config_dict(args, g.n, g.m, 1),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{per_step} trees per step ({cores} threads), the same graph"},
+                         "sample": f"{per_step} trees per step, one per thread on {cores} threads, the same graph "
+                                   f"(the workload's {args.K} trees per step are not all run)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -208,26 +249,77 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------- ours
+def bpp_timed(sb, K, steps, warmup, stream, world=1, rank=0, dist=None, clocks=None):
+    """`warmup` untimed then `steps` timed graphBpp steps of K trees (sample,
+    count, hash, cloud), bracketed by CUDA events on the library's stream."""
+    import torch
+
+    sb.cloud_reset(max_states=(warmup + steps + 2) * K + 64)
+    counts = torch.empty(K, dtype=torch.int32, device="cuda")
+    hashes = torch.empty(K, dtype=torch.int64, device="cuda")
+
+    # trees are independent: rank r takes its own tree ranges (weak scaling)
+    def step(i):
+        t0 = ((i * world) + rank) * K
+        sb.sample_trees(SEED, t0, K)
+        sb.frustration(counts, hashes)
+        return sb.cloud_insert()
+
+    for i in range(warmup):
+        step(i)
+    torch.cuda.synchronize()
+    sb.profile_read()
+    sb.profile(True)
+    if clocks:
+        clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(steps):
+        step(warmup + i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    sb.profile(False)
+    prof = sb.profile_read()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cl, fr_min = sb.cloud()
+    return {"ms_step": ms / steps, "prof": prof, "stats": sb.stats(), "clk": clk, "cloud": cl, "fr_min": fr_min}
+
+
+def stages(prof, steps):
+    return {k: round(v[0] / steps, 4) for k, v in prof.items() if v[1]}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    rank, world, local = dist_env()
+    workers = os.cpu_count() or 1
     if args.leg == "batch":
         import synth
 
         t = time.perf_counter()  # the process pool starts before any CUDA call
-        args.batch_graphs = list(synth.uneven_batch(count=args.graphs, workers=os.cpu_count() or 1))
+        args.batch_graphs = list(synth.uneven_batch(count=args.graphs, workers=workers))
         args.batch_gen_s = time.perf_counter() - t
-    if args.leg == "scale24":
-        import synth
-
+    elif args.leg != "quality":  # the quality leg draws its graph with the planted factions
         t = time.perf_counter()
-        args.scale_graph = synth.rmat_three_faction(scale=args.scale, m_target=1 << args.edges_log2,
-                                                    workers=os.cpu_count() or 1)
-        args.scale_gen_s = time.perf_counter() - t
+        args.graph = gen_graph(args.scale, args.edges_log2, args.factions, workers=workers)
+        args.gen_s = time.perf_counter() - t
+    side = args.leg == "bpp" and not args.no_extras and rank == 0 and args.workload == "rmat24" and not args.custom
+    if side:  # the 2^20-vertex graph of the side legs (graphL runs on it)
+        args.side_graph = gen_graph(20, 24, 2)
     import torch
 
-    rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -238,22 +330,23 @@ def main():
 
     if args.leg == "batch":
         return batch_leg(args, P)
-    if args.leg == "scale24":
-        return scale_leg(args, P)
     if args.leg == "quality":
         return quality_leg(args, P)
     if args.leg == "kruskal":
         return kruskal_leg(args, P)
-    n, u, v, s = workload(args)
+    n, u, v, s = args.graph
     stream = torch.cuda.current_stream()
     sb = P.SignedBal(local, stream=stream)
+    t = time.perf_counter()
     n1, m1, _ = sb.load_graph(n, u, v, s)
+    torch.cuda.synchronize()
+    ingest_s = time.perf_counter() - t
     if args.leg == "graphl":
         tuned = {"default": True}
         if not args.no_tune:
             from paper_2311_00869_gb300 import autotune
 
-            tuned = autotune.tune(sb, K=TREES, R=args.R)
+            tuned = autotune.tune(sb, K=1024, R=args.R)
         elif args.gl_lanes:
             sb.set_tuning(gl_lanes=args.gl_lanes)
             tuned = {"gl_lanes": args.gl_lanes}
@@ -265,59 +358,30 @@ def main():
         print(json.dumps(line), flush=True)
         sb.close()
         return 0
+    K = args.K
     tuned = {"default": True}
     if not args.no_tune:
         try:
             from paper_2311_00869_gb300 import autotune
 
-            tuned = autotune.tune(sb, K=TREES)
+            tuned = autotune.tune(sb, K=K)
         except Exception as e:  # tuning only changes speed
             tuned = {"error": repr(e)}
-    steps_total = args.warmup + args.steps
-    sb.cloud_reset(max_states=(steps_total + 2) * TREES + 64)
-    counts = torch.empty(TREES, dtype=torch.int32, device="cuda")
-    hashes = torch.empty(TREES, dtype=torch.int64, device="cuda")
-
-    # trees are independent: rank r takes its own tree ranges (weak scaling)
-    def step(i):
-        t0 = ((i * world) + rank) * TREES
-        sb.sample_trees(SEED, t0, TREES)
-        sb.frustration(counts, hashes)
-        return sb.cloud_insert()
-
-    for i in range(args.warmup):
-        step(i)
-    torch.cuda.synchronize()
-    sb.profile_read()
-    sb.profile(True)
-    clocks = ClockSampler(local)
-    clocks.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for i in range(args.steps):
-        step(args.warmup + i)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
-    sb.profile(False)
-    prof = sb.profile_read()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    ms_step = ms / args.steps
-    value = world * TREES * m1 / (ms_step / 1000.0)
+    peak_hps = None
+    try:
+        peak_hps = sb.hash_peak(1.0)  # measured ceiling of the BFS hash mix
+    except Exception:
+        pass
+    r = bpp_timed(sb, K, args.steps, args.warmup, stream, world, rank, dist, ClockSampler(local))
+    ms_step, prof = r["ms_step"], r["prof"]
+    value = world * K * m1 / (ms_step / 1000.0)
     launches = sum(c for _, c in prof.values())
-
-    cl, fr_min = sb.cloud()
-    extras = {"fr_min": int(fr_min), "distinct_states": int(cl["S"].shape[0]), "tuning": tuned,
-              "bfs_stats": sb.stats(), "trees_per_s": world * TREES / (ms_step / 1000.0)}
+    cl = r["cloud"]
+    extras = {"fr_min": int(r["fr_min"]), "distinct_states": int(cl["S"].shape[0]), "tuning": tuned,
+              "bfs_stats": r["stats"], "trees_per_s": world * K / (ms_step / 1000.0),
+              "generation_s": round(args.gen_s, 1), "ingest_s": round(ingest_s, 3)}
+    if args.factions == 3:
+        extras["negative_fraction"] = float((s < 0).mean())
     if dist:  # host-side merge of the rank clouds, after the timed region
         from paper_2311_00869_gb300 import shard
 
@@ -328,39 +392,65 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": config_dict(args, n1, m1, world),
-        "gpu_launches": launches, "clocks": clk,
-        "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
+        "gpu_launches": launches, "clocks": r["clk"], "stages_ms_per_step": stages(prof, args.steps),
     }
-    line["roofline"] = roofline(prof, n1, m1, TREES, extras["bfs_stats"], (clk or {}).get("sm_mhz"))
-    extras["roofline_score"] = roofline_family("score", prof, n1, m1, TREES)
+    line["roofline"] = roofline(prof, n1, m1, K, r["stats"], peak_hps)
+    extras["roofline_score"] = roofline_family("score", prof, n1, m1, K)
     if not args.no_extras and rank == 0:
         try:
-            extras.update(plain_leg(sb, m1))
-        except Exception as e:  # a failing side leg must not hide the main number
-            extras["plain_error"] = repr(e)
-        try:
-            from paper_2311_00869_gb300 import autotune
-
-            extras["graphl_tuning"] = autotune.tune(sb, K=TREES, R=256)
-            extras.update(graphl_leg(P, sb, n1, m1))
-        except Exception as e:
-            extras["graphl_error"] = repr(e)
-        try:
-            line["e2e"] = e2e_leg(P, sb, n, u, v, s)
+            line["e2e"] = e2e_leg(P, sb, n, u, v, s, K)
         except Exception as e:
             line["e2e"] = {"error": repr(e)}
+        g = None
         try:
             g = oracle_graph(n, u, v, s)
-            line["cpu_baseline"] = cpu_baseline(g)
+            line["cpu_baseline"] = cpu_baseline(sb, g)
         except Exception as e:
             line["cpu_baseline"] = {"error": repr(e)}
+        del g
+    sb.close()
+    torch.cuda.empty_cache()
+    if side:
+        try:
+            extras["rmat20_2faction_K1024"] = side_legs(P, args, stream, peak_hps)
+        except Exception as e:  # a failing side leg must not hide the main number
+            extras["rmat20_error"] = repr(e)
+        try:
+            extras["plain_er1000_K64"] = plain_leg_er(P, stream)
+        except Exception as e:
+            extras["plain_er1000_error"] = repr(e)
     line["extras"] = extras
     if rank == 0:
         print(json.dumps(line), flush=True)
-    sb.close()
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def side_legs(P, args, stream, peak_hps, K=1024, steps=10, warmup=3):
+    """The 2^20-vertex two-faction graph: its graphBpp line (1024 trees per
+    step), plain against batched on 64 of its trees, and graphL with R = 256
+    start points for 500 steps against one start point per launch."""
+    n, u, v, s = args.side_graph
+    sb = P.SignedBal(0, stream=stream)
+    try:
+        n1, m1, _ = sb.load_graph(n, u, v, s)
+        from paper_2311_00869_gb300 import autotune
+
+        tuned = autotune.tune(sb, K=K)
+        r = bpp_timed(sb, K, steps, warmup, stream)
+        out = {"n": n1, "m": m1, "trees_per_step": K, "steps": steps, "ms_per_step": r["ms_step"],
+               "edge_evals_per_s": K * m1 / (r["ms_step"] / 1000.0), "trees_per_s": K / (r["ms_step"] / 1000.0),
+               "stages_ms_per_step": stages(r["prof"], steps), "bfs_stats": r["stats"], "tuning": tuned,
+               "roofline": roofline_family("bfs", r["prof"], n1, m1, K, r["stats"], peak_hps),
+               "roofline_score": roofline_family("score", r["prof"], n1, m1, K),
+               "fr_min": int(r["fr_min"])}
+        out["plain_vs_batched"] = plain_leg(sb, m1)
+        out["graphl_tuning"] = autotune.tune(sb, K=K, R=256)
+        out["graphl"] = graphl_leg(P, sb, n1, m1, R=256, steps=500, plain_inits=4)
+    finally:
+        sb.close()
+    return out
 
 
 def _src_digest(paths):
@@ -398,9 +488,7 @@ def _traffic_bytes():
 
 
 NCU_TRAFFIC_BYTES = _traffic_bytes()
-ALU_LANES_PER_SM = 128  # INT32-capable lanes per SM (4 partitions x 32)
-NUM_SMS = 152
-OPS_PER_HASH = 11  # (u ^ y) + key: 2, the 32-bit finaliser: 8, compare: 1
+OPS_PER_HASH = 10  # per hashed candidate: + tree salt (1), the 32-bit finaliser (8), running minimum (1)
 
 
 def _peaks():
@@ -410,12 +498,26 @@ def _peaks():
         return {}
 
 
-def roofline_family(fam, prof, n, m, K, stats=None, sm_mhz=None):
+def _derived_alu_peak():
+    """SMs x 128 INT32 lanes x the largest SM clock, in Gop/s (an upper bound:
+    the finaliser's two multiplies do not issue at that rate)."""
+    try:
+        import torch
+
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+    except Exception:
+        sms = 152
+    mhz = float(_peaks().get("sm_max_mhz", 2070.0))
+    return sms * 128 * mhz * 1e6 / 1e9, f"derived: {sms} SMs x 128 INT32 lanes x {mhz:.0f} MHz"
+
+
+def roofline_family(fam, prof, n, m, K, stats=None, peak_hps=None):
     """Roofline of one kernel family: HBM-bound families against the measured
     copy bandwidth with their algorithmic bytes per launch; the BFS against
-    the integer-ALU peak (SMs x INT32 lanes x SM clock) with the parent-key
-    hashes the kernel computes per launch (every candidate of every open tree,
-    as counted by the kernel)."""
+    the measured rate of its own hash mix (sb_hash_peak: the add, finaliser
+    and minimum of one hashed candidate, on independent chains over the whole
+    GPU), with the candidates the kernel hashes per launch (every candidate
+    of every open tree, as counted by the kernel)."""
     peaks = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     src = "measured" if "hbm_gbs" in peaks else "fallback"
@@ -427,14 +529,19 @@ def roofline_family(fam, prof, n, m, K, stats=None, sm_mhz=None):
         if not stats or not stats.get("bfs_launches"):
             return None
         hashes = (stats["hashed_candidates"] + stats["hashed_candidates_split_rows"]) / stats["bfs_launches"]
-        mhz = 2070.0
-        peak = NUM_SMS * ALU_LANES_PER_SM * mhz * 1e6 / 1e9  # Gop/s at the maximum SM clock
         achieved = OPS_PER_HASH * hashes / avg_s / 1e9
-        return {"bound": "alu", "kernel": "k_bfs", "achieved": achieved, "peak": peak,
-                "peak_source": f"derived: {NUM_SMS} SMs x {ALU_LANES_PER_SM} INT32 lanes x {mhz:.0f} MHz",
+        derived, dsrc = _derived_alu_peak()
+        if peak_hps:
+            peak = OPS_PER_HASH * peak_hps / 1e9
+            psrc = ("measured: sb_hash_peak, the BFS's per-candidate hash mix (salt add, fmix32, min) on 8 "
+                    "independent chains per thread over a full grid, 1 s, CUDA events")
+        else:
+            peak, psrc = derived, dsrc
+        return {"bound": "alu", "kernel": "k_bfs", "achieved": achieved, "peak": peak, "peak_source": psrc,
                 "unit": "Gop/s", "frac": achieved / peak, "traffic": NCU_TRAFFIC_BYTES.get("bfs"),
+                "ops_per_hash": OPS_PER_HASH, "hashes_per_launch": hashes,
                 "algorithmic_ops_per_launch": OPS_PER_HASH * hashes, "avg_launch_ms": 1000 * avg_s,
-                "launches": launches, "sm_mhz_median": sm_mhz}
+                "launches": launches, "derived_peak": derived, "derived_peak_source": dsrc}
     W = (K + 63) // 64
     per_launch = {
         # edge stream (8 B per edge) + every label word read once (n x W x 8 B) + counts
@@ -451,41 +558,71 @@ def roofline_family(fam, prof, n, m, K, stats=None, sm_mhz=None):
             "avg_launch_ms": 1000 * avg_s, "launches": launches}
 
 
-def roofline(prof, n, m, K, stats=None, sm_mhz=None):
+def roofline(prof, n, m, K, stats=None, peak_hps=None):
     """Roofline object of the dominant kernel family."""
     fam = max(prof, key=lambda k: prof[k][0])
-    r = roofline_family(fam, prof, n, m, K, stats, sm_mhz)
+    r = roofline_family(fam, prof, n, m, K, stats, peak_hps)
     return r if r is not None else {"bound": "hbm", "kernel": fam, "achieved": None, "peak": None, "unit": "GB/s",
                                     "frac": None, "traffic": None}
 
 
-def plain_leg(sb, m):
-    """The same 64 trees, one tree per launch (plain) vs one 64-tree launch."""
+def _same_cloud(a, b):
+    return all(np.array_equal(a[k], b[k]) for k in ("hash", "S", "count", "first_tree"))
+
+
+def plain_leg(sb, m, trees=64, reps=3, t0=50_000_000):
+    """The same `trees` trees, one tree per launch (plain: sample, count, cloud
+    per tree) against one batched launch; each arm warmed up once, then timed
+    `reps` times with CUDA events; the two clouds must be equal (hash, S,
+    count, first tree)."""
     import torch
 
-    sb.cloud_reset(max_states=8192)
-    t0 = 50_000_000
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    for i in range(64):
-        sb.sample_trees(SEED, t0 + i, 1)
+    def plain():
+        sb.cloud_reset(max_states=trees + 64)
+        for i in range(trees):
+            sb.sample_trees(SEED, t0 + i, 1)
+            sb.frustration()
+            sb.cloud_insert()
+
+    def batched():
+        sb.cloud_reset(max_states=trees + 64)
+        sb.sample_trees(SEED, t0, trees)
         sb.frustration()
         sb.cloud_insert()
-    torch.cuda.synchronize()
-    plain = time.perf_counter() - t
-    c_plain, _ = sb.cloud()
-    sb.cloud_reset(max_states=8192)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    sb.sample_trees(SEED, t0, 64)
-    counts, _ = sb.frustration()
-    sb.cloud_insert()
-    torch.cuda.synchronize()
-    batched = time.perf_counter() - t
-    c_b, fr_b = sb.cloud()
-    same = bool(np.array_equal(c_plain["S"], c_b["S"]) and np.array_equal(c_plain["count"], c_b["count"]))
-    return {"plain_edge_evals_per_s": 64 * m / plain, "batched64_edge_evals_per_s": 64 * m / batched,
-            "plain_vs_batched_same_cloud": same, "plain64_fr_min": int(c_plain["S"].min())}
+
+    out = {}
+    for name, fn in (("plain", plain), ("batched", batched)):
+        fn()  # warm-up (buffers sized for this arm)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = (e0.elapsed_time(e1) / reps, sb.cloud()[0])
+    return {"trees": trees, "plain_ms": out["plain"][0], "batched_ms": out["batched"][0],
+            "plain_edge_evals_per_s": trees * m / (out["plain"][0] / 1000.0),
+            "batched_edge_evals_per_s": trees * m / (out["batched"][0] / 1000.0),
+            "same_cloud": bool(_same_cloud(out["plain"][1], out["batched"][1])),
+            "fr_min": int(out["batched"][1]["S"].min())}
+
+
+def plain_leg_er(P, stream):
+    """The small plain workload: Erdos-Renyi n = 1,000, m = 5,000, 20 %
+    negative, K = 64 trees from seed 0, one tree per launch, against the same
+    64 trees in one launch."""
+    import synth
+
+    n, u, v, s = synth.er_graph()
+    sb = P.SignedBal(0, stream=stream)
+    try:
+        n1, m1, _ = sb.load_graph(n, u, v, s)
+        res = plain_leg(sb, m1, trees=64, reps=5, t0=0)
+        res.update({"n": n1, "m": m1})
+    finally:
+        sb.close()
+    return res
 
 
 def graphl_leg(P, sb, n, m, R=256, steps=50, alpha=0.05, plain_inits=0):
@@ -536,7 +673,7 @@ def graphl_leg(P, sb, n, m, R=256, steps=50, alpha=0.05, plain_inits=0):
     return res
 
 
-def e2e_leg(P, sb, n, u, v, s, steps=3):
+def e2e_leg(P, sb, n, u, v, s, K, steps=3):
     """Through the C ABI with host buffers: per step the COO goes host -> device
     from pinned memory, is ingested, K trees are sampled, and the counts,
     hashes and cloud come back to host memory."""
@@ -545,23 +682,26 @@ def e2e_leg(P, sb, n, u, v, s, steps=3):
     pu = torch.from_numpy(u).pin_memory()
     pv = torch.from_numpy(v).pin_memory()
     ps = torch.from_numpy(s).pin_memory()
-    hc = torch.empty(TREES, dtype=torch.int32).pin_memory()
-    hh = torch.empty(TREES, dtype=torch.int64).pin_memory()
+    hc = torch.empty(K, dtype=torch.int32).pin_memory()
+    hh = torch.empty(K, dtype=torch.int64).pin_memory()
     m1 = 0
+    n_states = 0
+    sb.cloud_reset(max_states=K + 64)  # room for one step's trees (the timed line kept every step's)
     torch.cuda.synchronize()
     t = time.perf_counter()
     for i in range(steps):
         _, m1, _ = sb.load_graph(n, pu, pv, ps)
-        sb.sample_trees(SEED, 90_000_000 + i * TREES, TREES)
+        sb.sample_trees(SEED, 90_000_000 + i * K, K)
         sb.frustration(hc, hh)
         cl, fr = sb.cloud()
+        n_states = int(cl["S"].shape[0])
     torch.cuda.synchronize()
     el = time.perf_counter() - t
     h2d = u.nbytes + v.nbytes + s.nbytes
-    d2h = hc.numel() * 4 + hh.numel() * 8 + int(cl["S"].shape[0]) * 24
-    return {"value": steps * TREES * m1 / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "includes": "H2D of the COO, ingest, sample, count, cloud, D2H"}
-
+    d2h = hc.numel() * 4 + hh.numel() * 8 + n_states * 24
+    return {"value": steps * K * m1 / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": steps,
+            "includes": "H2D of the COO, ingest, sample, count, cloud, D2H"}
 
 
 def batch_cpu_baseline(graphs, K, count=64):
@@ -665,7 +805,7 @@ def quality_leg(args, P, K_total=4096, R=256, steps=500, alpha=0.05):
     if not args.no_tune:
         from paper_2311_00869_gb300 import autotune
 
-        autotune.tune(sb, K=TREES, R=R)
+        autotune.tune(sb, K=args.K, R=R)
     # planted state on the cleaned graph: edges whose sign disagrees with it
     cu, cv, cneg = (t.cpu().numpy() for t in sb.graph_edges())
     inv = np.empty(n1, np.int64)
@@ -675,11 +815,11 @@ def quality_leg(args, P, K_total=4096, R=256, steps=500, alpha=0.05):
     mins, counts_all = {}, []
     t0 = 0
     while t0 < K_total:
-        sb.sample_trees(SEED, t0, TREES)
+        sb.sample_trees(SEED, t0, args.K)
         c, _ = sb.frustration()
         counts_all.append(c.cpu().numpy())
         sb.cloud_insert()
-        t0 += TREES
+        t0 += args.K
     cs = np.concatenate(counts_all)
     for k in (64, 256, 1024, 4096):
         if k <= K_total:
@@ -694,7 +834,7 @@ def quality_leg(args, P, K_total=4096, R=256, steps=500, alpha=0.05):
         if r <= R:
             gl[str(r)] = [int(Ft[st, :r].min()) for st in range(0, steps, 50)] + [int(Ff[:r].min())]
     line = {"leg": "quality", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n1, "m": m1, "graphl_R": R, "graphl_steps": steps,
+            "config": {"workload": workload_name(args), "n": n1, "m": m1, "graphl_R": R, "graphl_steps": steps,
                        "graphl_alpha": alpha},
             "planted_state_frustration": planted,
             "graphbpp_min_S_after_K_trees": mins, "graphbpp_distinct_states": int(cl["S"].shape[0]),
@@ -712,11 +852,11 @@ def kruskal_leg(args, P):
     Kruskal trees on the host cores."""
     import torch
 
-    n, u, v, s = workload(args)
+    n, u, v, s = args.graph
     stream = torch.cuda.current_stream()
     sb = P.SignedBal(0, stream=stream)
     n1, m1, _ = sb.load_graph(n, u, v, s)
-    K = TREES
+    K = args.K
     steps_total = args.warmup + args.steps
 
     def run(sample):
@@ -763,104 +903,6 @@ def kruskal_leg(args, P):
         line["cpu_baseline"] = {"value": cores * g.m / el, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{cores} Kruskal trees (sort, union-find, labels, count, hash), "
                                           f"{cores} threads, {el:.1f} s"}
-    print(json.dumps(line), flush=True)
-    sb.close()
-    return 0
-
-
-def scale_cpu_baseline(sb, n, u, v, s, K, each=8):
-    """The oracle on trees [0, each) and [K - each, K) of the paper-scale
-    graph on all host cores (the rate is extrapolated to all K trees), and a
-    bit-for-bit check of those trees' counts and hashes against the GPU."""
-    import oracle as O
-
-    cores = os.cpu_count() or 1
-    t = time.perf_counter()
-    g = O.clean_graph(n, u, v, s)
-    clean_s = time.perf_counter() - t
-    trees = list(range(each)) + list(range(K - each, K))
-    t = time.perf_counter()
-    with ThreadPoolExecutor(max_workers=cores) as ex:
-        refs = list(ex.map(lambda tt: O.sample(g, SEED, tt, 1, want_labels=False), trees))
-    el = time.perf_counter() - t
-    sb.sample_trees(SEED, 0, K)
-    counts, hashes = sb.frustration()
-    counts, hashes = counts.cpu().numpy(), hashes.cpu().numpy().view(np.uint64)
-    same = all(counts[tt] == r["counts"][0] and hashes[tt] == r["hashes"][0] for tt, r in zip(trees, refs))
-    return {"value": len(trees) * g.m / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"trees [0,{each}) and [{K - each},{K}) on {cores} threads, {el:.1f} s "
-                      f"(rate extrapolated to {K} trees); cleaning the graph took {clean_s:.1f} s",
-            "bit_exact_on_sample": bool(same)}
-
-
-def scale_leg(args, P):
-    """Paper-scale graphBpp: R-MAT with 2^24 vertex ids and 2^27 distinct
-    undirected edges, three planted factions (94.8 / 2.6 / 2.6 %, inter-faction
-    edges negative) with 15 % sign noise; each step grows 4096 trees (64
-    words), scores them and adds them to the cloud."""
-    import torch
-
-    n, u, v, s = args.scale_graph
-    sb = P.SignedBal(0)
-    t = time.perf_counter()
-    n1, m1, _ = sb.load_graph(n, u, v, s)
-    torch.cuda.synchronize()
-    ingest_s = time.perf_counter() - t
-    K = 4096
-    tuned = {"default": True}
-    if not args.no_tune:
-        from paper_2311_00869_gb300 import autotune
-
-        tuned = autotune.tune(sb, K=K)
-    sb.cloud_reset(max_states=(args.warmup + args.steps) * K + 64)
-    counts = torch.empty(K, dtype=torch.int32, device="cuda")
-    hashes = torch.empty(K, dtype=torch.int64, device="cuda")
-
-    def step(i):
-        sb.sample_trees(SEED, i * K, K)
-        sb.frustration(counts, hashes)
-        return sb.cloud_insert()
-
-    for i in range(args.warmup):
-        step(i)
-    torch.cuda.synchronize()
-    sb.profile_read()
-    sb.profile(True)
-    clocks = ClockSampler(0)
-    clocks.start()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    for i in range(args.steps):
-        step(args.warmup + i)
-    ev1.record()
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    sb.profile(False)
-    prof = sb.profile_read()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    stats = sb.stats()
-    cl, fr_min = sb.cloud()
-    line = {
-        "leg": "scale24", "metric": "graphBpp edge-evals/s (trees x |E| / s), batched", "value": K * m1 / (ms / 1e3),
-        "unit": "edge-evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": f"rmat{args.scale}_3faction_K4096", "n": n1, "m": m1, "trees_per_step": K,
-                   "graph": f"R-MAT scale {args.scale}, 2^{args.edges_log2} undirected edges, three factions + "
-                            "15% sign noise, LCC",
-                   "generation_s": args.scale_gen_s, "ingest_s": ingest_s},
-        "gpu_launches": sum(c for _, c in prof.values()), "clocks": clk,
-        "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
-        "roofline": roofline(prof, n1, m1, K, stats, (clk or {}).get("sm_mhz")),
-        "roofline_score": roofline_family("score", prof, n1, m1, K),
-        "extras": {"fr_min": int(fr_min), "distinct_states": int(cl["S"].shape[0]), "bfs_stats": stats, "tuning": tuned,
-                   "negative_fraction": float((s < 0).mean())},
-    }
-    if not args.no_extras:
-        try:
-            line["cpu_baseline"] = scale_cpu_baseline(sb, n, u, v, s, K)
-        except Exception as e:  # the baseline must not hide the main number
-            line["cpu_baseline"] = {"error": repr(e)}
     print(json.dumps(line), flush=True)
     sb.close()
     return 0

@@ -109,12 +109,27 @@ sb_status sb_profile_read(sb_ctx* ctx, double* ms_out, int64_t* launches_out);
                              of two in [1, 32]; used when it is at most twice
                              the launch's words rounded up to a power of two
                              (0 or otherwise: that power of two)
-   Results never depend on them.  sb_get_tuning returns the current value. */
+   SB_TUNE_WAIT_US           limit of every bounded device wait (the BFS grid
+                             barrier between levels, the scorer's tile
+                             copies), in microseconds at the device's SM
+                             clock, 1 .. 6e7 (0 = 10 s).  A wait that runs
+                             out makes its kernel stop early and the next
+                             sb_label / sb_frustration return SB_ERR_TIMEOUT;
+                             the context stays usable.
+   SB_TUNE_STALL_TEST        1: the grid barriers of the next sb_sample_trees
+                             call wait for one block more than the launch
+                             has, so that every barrier wait runs out (a
+                             test of the timeout path; no fault, nothing is
+                             left running).  Reset to 0 by that call.
+   Results never depend on the first four.  sb_get_tuning returns the
+   current value. */
 #define SB_TUNE_BFS_WORDS 0
 #define SB_TUNE_SCORE_BLOCKS_SM 1
 #define SB_TUNE_GL_LANES 2
 #define SB_TUNE_BFS_GROUP 3
-#define SB_TUNE_N 4
+#define SB_TUNE_WAIT_US 4
+#define SB_TUNE_STALL_TEST 5
+#define SB_TUNE_N 6
 sb_status sb_set_tuning(sb_ctx* ctx, int32_t knob, int64_t value);
 sb_status sb_get_tuning(sb_ctx* ctx, int32_t knob, int64_t* value);
 
@@ -127,6 +142,15 @@ sb_status sb_get_tuning(sb_ctx* ctx, int32_t knob, int64_t* value);
    Synchronises the stream. */
 #define SB_STATS_N 6
 sb_status sb_stats(sb_ctx* ctx, int64_t* out, int32_t n);
+
+/* Measures the integer-ALU ceiling of the BFS's hash work on the context's
+   device: a full grid evaluates, for `seconds` (0 < seconds <= 60), the
+   parent-key hash of sb_sample_trees (one add of the tree salt, the 32-bit
+   MurmurHash3 finaliser, one running minimum) on independent chains and
+   nothing else, timed with CUDA events on the context's stream.
+   *hashes_per_s_out (host) receives hashes per second.  Synchronous; for
+   benchmarks (the roofline of the BFS sampler). */
+sb_status sb_hash_peak(sb_ctx* ctx, double seconds, double* hashes_per_s_out);
 
 /* ------------------------------------------------------------ graph ingest */
 
@@ -352,9 +376,15 @@ sb_status sb_graphL_round(sb_ctx* ctx, const float* gamma, int32_t R, int32_t* F
  *   cuda_stream: cudaStream_t (NULL = legacy default stream).
  * Limits: 1 <= R <= 1024 and 0 <= m < 2^31, else SB_ERR_ARG and nothing runs.
  * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) and should come before any stream capture.  All
- * calls on a device share the scratch and it keeps the last call's contents:
- * calls that overlap on the GPU race and must be serialised by the caller.
+ * (cudaGetSymbolAddress) and should come before any stream capture.  That
+ * address is kept per device for the life of the process, so every call must
+ * run in the device's primary context (the CUDA runtime's own); a driver
+ * context made current by the caller, or a cudaDeviceReset between calls,
+ * is not supported.  All calls on a device share the scratch and it keeps the
+ * last call's contents: calls that overlap on the GPU race and must be
+ * serialised by the caller.  A CUDA error already pending when the call is
+ * made (from the caller's earlier work) is left in place and the call returns
+ * SB_ERR_CUDA without launching anything.
  */
 sb_status sb_graphL_fwd_static(const int32_t* edges, int64_t m, const float* gamma, int32_t R, float* loss_out,
                                int32_t* F_out, void* cuda_stream);

@@ -286,7 +286,8 @@ class SignedBal:
     def sync(self):
         self._check(self.lib.sb_sync(self.h))
 
-    TUNE_KNOBS = {"bfs_words": 0, "score_blocks_sm": 1, "gl_lanes": 2, "bfs_group": 3}
+    TUNE_KNOBS = {"bfs_words": 0, "score_blocks_sm": 1, "gl_lanes": 2, "bfs_group": 3, "wait_us": 4,
+                  "stall_test": 5}
 
     def set_tuning(self, **knobs):
         for k, v in knobs.items():
@@ -299,6 +300,12 @@ class SignedBal:
             self._check(self.lib.sb_get_tuning(self.h, i, ctypes.byref(v)))
             out[k] = v.value
         return out
+
+    def hash_peak(self, seconds=1.0):
+        """Measured hashes/s of the BFS parent-key hash mix on this GPU."""
+        out = ctypes.c_double()
+        self._check(self.lib.sb_hash_peak(self.h, float(seconds), ctypes.byref(out)))
+        return out.value
 
     def stats(self):
         """Work counters of the last sample_trees call."""

@@ -27,6 +27,7 @@ SIGNATURES = {
     "sb_profile": (i32, [P, ctypes.c_int]),
     "sb_profile_read": (i32, [P, P, P]),
     "sb_stats": (i32, [P, P, i32]),
+    "sb_hash_peak": (i32, [P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     "sb_set_tuning": (i32, [P, i32, i64]),
     "sb_get_tuning": (i32, [P, i32, P]),
     "sb_load_graph": (i32, [P, i64, i64, P, P, P, u32, ctypes.POINTER(i64), ctypes.POINTER(i64), P]),

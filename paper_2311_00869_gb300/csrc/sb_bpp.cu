@@ -28,7 +28,6 @@
 #define BSLOT(o, t) ((o) * 65 + (t))  // 32-bit minima / winner ids
 #define LSLOT(o, t) ((o) * 68 + (t))  // winner label bytes
 #define KSLOT(w, t) ((w) * 65 + (t))  // tree salts of word w
-#define BAR_LIMIT_CYCLES (4ll * 1000 * 1000 * 1000)  // ~2 s at 2 GHz
 
 struct BfsArgs {
     const sb_bfs_item* items;
@@ -50,12 +49,15 @@ struct BfsArgs {
     uint64_t S;         // seed key
     int64_t tree0;      // global index of batch tree 0
     const int32_t* vgoff;  // first vertex of each vertex's graph (batches), or null
+    long long wait;        // SM cycles a barrier wait may take before it reports a timeout
+    unsigned bar_extra;    // arrivals a barrier expects beyond the launch's blocks (0; 1 tests the timeout path)
 };
 
 // ----------------------------------------------------------- grid barrier
 // Cooperative launch makes every block resident; the wait is still bounded
-// and reports a timeout through sync[6] instead of hanging.
-__device__ __forceinline__ void grid_barrier(uint32_t* sync, unsigned nblocks)
+// (`limit` SM cycles) and reports a timeout through sync[6] instead of
+// hanging.  `nblocks` is the number of arrivals that open the barrier.
+__device__ __forceinline__ void grid_barrier(uint32_t* sync, unsigned nblocks, long long limit)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -71,7 +73,7 @@ __device__ __forceinline__ void grid_barrier(uint32_t* sync, unsigned nblocks)
             long long t0 = clock64();
             while (*gen == g) {
                 __nanosleep(40);
-                if (clock64() - t0 > BAR_LIMIT_CYCLES) {
+                if (clock64() - t0 > limit) {
                     atomicOr(sync + 6, 1u);
                     break;
                 }
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
     const unsigned gmask = group_mask(G);
     const int64_t groups_total = (int64_t)gridDim.x * (BD / G);
     const int64_t group_id = (int64_t)blockIdx.x * (BD / G) + tid / G;
-    const unsigned nblocks = gridDim.x;
+    const unsigned nblocks = gridDim.x + A.bar_extra;
 
     for (int i = tid; i < A.Wb * 64; i += BD)
         akey[KSLOT(i >> 6, i & 63)] = (uint32_t)sb_tree_key(A.S, A.tree0 + 64 * (int64_t)A.w0 + i);
@@ -425,7 +427,7 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
 
         // ---- phase B: resolve split rows
         if (A.n_hubs > 0) {
-            grid_barrier(A.sync, nblocks);
+            grid_barrier(A.sync, nblocks, A.wait);
             for (int64_t h = group_id; h < A.n_hubs; h += groups_total) {
                 const int32_t v = A.hub_vertex[h];
                 const int32_t d = A.done[v];
@@ -469,7 +471,7 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
             s_any = 0;
             if (blockIdx.x == 0) A.sync[(L + 1) % 3] = 0;
         }
-        grid_barrier(A.sync, nblocks);
+        grid_barrier(A.sync, nblocks, A.wait);
         // one reader per block, so that every thread of a block leaves the
         // level loop at the same level
         if (tid == 0) {
@@ -724,6 +726,8 @@ static sb_status run_bfs(sb_ctx* c, int w0, int Wb, int32_t* parents)
     A.S = sb_seed_key(c->seed);
     A.tree0 = c->tree_begin;
     A.vgoff = c->batch_G > 0 ? c->vgoff : nullptr;
+    A.wait = sb_wait_cycles(c);
+    A.bar_extra = c->tune[SB_TUNE_STALL_TEST] ? 1u : 0u;
     void* args[] = {&A};
     {
         SbProf prof(c, SB_PROF_BFS);
@@ -828,10 +832,13 @@ extern "C" sb_status sb_sample_trees(sb_ctx* c, uint64_t seed, int64_t tree_begi
     if (!c->done) c->done = (int32_t*)sb_dalloc(c, sizeof(int32_t) * (size_t)n);
     if (!c->bfs_cap_words || !c->done)
         return sb_fail(c, SB_ERR_OOM, "BFS batch storage (n=%lld, K=%lld)", (long long)n, (long long)K);
-    for (int w0 = 0; w0 < W; w0 += WL) {
+    sb_status st = SB_OK;
+    for (int w0 = 0; w0 < W && st == SB_OK; w0 += WL) {
         int Wb = W - w0 < WL ? W - w0 : WL;
-        SB_TRY(run_bfs(c, w0, Wb, parents_out));
+        st = run_bfs(c, w0, Wb, parents_out);
     }
+    c->tune[SB_TUNE_STALL_TEST] = 0;  // a test of the timeout path covers one call
+    SB_TRY(st);
     return sb_batch_end(c);
 }
 

@@ -287,6 +287,10 @@ extern "C" sb_status sb_create(sb_ctx** out, int device, void* cuda_stream)
         delete c;
         return SB_ERR_CUDA;
     }
+    if (cudaDeviceGetAttribute(&c->clock_khz, cudaDevAttrClockRate, device) != cudaSuccess || c->clock_khz <= 0) {
+        cudaGetLastError();
+        c->clock_khz = 2070000;  // the GB300's largest SM clock
+    }
     *out = c;
     return SB_OK;
 }
@@ -331,8 +335,16 @@ extern "C" sb_status sb_set_tuning(sb_ctx* c, int32_t knob, int64_t value)
         return sb_fail(c, SB_ERR_ARG, "graphL lanes must be 8 or 32");
     if (knob == SB_TUNE_BFS_GROUP && (value > 32 || (value & (value - 1)) != 0))
         return sb_fail(c, SB_ERR_ARG, "BFS group must be a power of two <= 32");
+    if (knob == SB_TUNE_WAIT_US && value > 60000000) return sb_fail(c, SB_ERR_ARG, "wait limit at most 6e7 us");
+    if (knob == SB_TUNE_STALL_TEST && value > 1) return sb_fail(c, SB_ERR_ARG, "stall test is 0 or 1");
     c->tune[knob] = value;
     return SB_OK;
+}
+
+long long sb_wait_cycles(const sb_ctx* c)
+{
+    const long long us = c->tune[SB_TUNE_WAIT_US] > 0 ? (long long)c->tune[SB_TUNE_WAIT_US] : SB_WAIT_DEFAULT_US;
+    return us * (long long)c->clock_khz / 1000;
 }
 
 extern "C" sb_status sb_get_tuning(sb_ctx* c, int32_t knob, int64_t* value)

@@ -701,6 +701,9 @@ extern "C" sb_status sb_graphL_fwd_static(const int32_t* edges, int64_t m, const
 {
     if (R < 1 || R > GL_STATIC_RMAX || m < 0 || m >= (1ll << 31) || !gamma || !loss_out || (m > 0 && !edges))
         return SB_ERR_ARG;
+    // an error left pending by the caller's own earlier work is not ours to
+    // clear; refuse to run rather than report it as this call's failure
+    if (cudaPeekAtLastError() != cudaSuccess) return SB_ERR_CUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
         cudaGetLastError();
@@ -729,6 +732,7 @@ extern "C" sb_status sb_graphL_fwd_static(const int32_t* edges, int64_t m, const
         return SB_ERR_CUDA;
     }
     k_gl_fwd<<<GL_STATIC_BLOCKS, GL_THREADS, 0, st>>>((const int2*)edges, m, gamma, R, red, Facc);
+    if (cudaGetLastError() != cudaSuccess) return SB_ERR_CUDA;
     k_gl_fwd_final<<<(unsigned)sb_cdiv(R, 256), 256, 0, st>>>(red, GL_STATIC_BLOCKS, R, m, loss_out, Facc, F_out);
     if (cudaGetLastError() != cudaSuccess) return SB_ERR_CUDA;
     return SB_OK;

@@ -83,6 +83,7 @@ struct sb_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int num_sms = 0;
+    int clock_khz = 0;             // SM clock (kHz) for bounded device waits
     sb_alloc_fn alloc = nullptr;
     sb_free_fn free_fn = nullptr;
     void* alloc_user = nullptr;
@@ -190,7 +191,7 @@ struct sb_ctx {
     size_t tmp_cap = 0;
 
     // tuning knobs (SB_TUNE_*)
-    int64_t tune[SB_TUNE_N] = {0, 0, 0, 0};
+    int64_t tune[SB_TUNE_N] = {0};
 
     // profiling: per-family launch counts, optional CUDA-event timing
     int prof_on = 0;
@@ -213,6 +214,9 @@ sb_status sb_copy_out(sb_ctx* c, void* dst, const void* src_dev, size_t bytes);
 sb_status sb_after_launch(sb_ctx* c, const char* what);
 void sb_prof_begin(sb_ctx* c, cudaEvent_t* a);
 void sb_prof_end(sb_ctx* c, int fam, cudaEvent_t a);
+// SM cycles of the bounded device waits (SB_TUNE_WAIT_US; 10 s by default)
+long long sb_wait_cycles(const sb_ctx* c);
+#define SB_WAIT_DEFAULT_US 10000000ll
 
 // Scope that attributes the kernel launches inside it to one family and,
 // when profiling is on, brackets them with CUDA events on the ctx stream.

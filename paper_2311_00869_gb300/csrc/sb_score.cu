@@ -27,7 +27,6 @@ static int score_group_for(int Wb)
 #define SC_FAST_BATCH 1                  // whole 8-edge batches without per-edge checks
 #define SC_RIPPLE_EXIT 1                 // stop the ripple when no carry is left
 #define SC_FLUSH ((1 << SC_PLANES) - 1)  // batches of 8 edges between flushes
-#define SC_WAIT_CYCLES (4ll * 1000 * 1000 * 1000)  // ~2 s at 2 GHz
 
 __device__ __forceinline__ void csa(uint64_t& h, uint64_t& l, uint64_t a, uint64_t b, uint64_t c)
 {
@@ -45,6 +44,8 @@ struct ScoreArgs {
     int64_t KP;           // count slots per graph
     uint32_t* counts;     // [graph * KP + 64 * word + bit]
     uint32_t* err;        // bit 0 set when a tile copy did not arrive in time
+    long long wait;       // SM cycles a tile wait may take before it reports a timeout
+    long long drain;      // SM cycles the copies still in flight get before a failed block exits
 };
 
 struct ScoreAcc {
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(SC_THREADS, SEG ? 3 : 4) k_score(ScoreArgs A)
     for (int64_t t = t0; t < t1; t++) {
         const int buf = (int)((t - t0) & 1);
         if (tid == 0 && t + 1 < t1) issue(t + 1, buf ^ 1);  // read by nobody since the last barrier
-        if (!sb_mbar_wait(&bar[buf], (uint32_t)(((t - t0) >> 1) & 1), SC_WAIT_CYCLES)) atomicOr(&s_fail, 1u);
+        if (!sb_mbar_wait(&bar[buf], (uint32_t)(((t - t0) >> 1) & 1), A.wait)) atomicOr(&s_fail, 1u);
         __syncthreads();
         if (s_fail) {
             tf = t;
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(SC_THREADS, SEG ? 3 : 4) k_score(ScoreArgs A)
             atomicOr(A.err, 1u);
             // let the copies still in flight land (bounded) before the block exits
             for (int64_t t = tf; t < min(tf + 2, t1); t++)
-                (void)sb_mbar_wait(&bar[(t - t0) & 1], (uint32_t)(((t - t0) >> 1) & 1), SC_WAIT_CYCLES);
+                (void)sb_mbar_wait(&bar[(t - t0) & 1], (uint32_t)(((t - t0) >> 1) & 1), A.drain);
         }
         return;
     }
@@ -269,6 +270,8 @@ sb_status sb_score_batch(sb_ctx* c)
         A.KP = 64 * (int64_t)c->W;
         A.counts = (uint32_t*)c->counts;
         A.err = c->sync + 28;
+        A.wait = sb_wait_cycles(c);
+        A.drain = std::max(A.wait, SB_WAIT_DEFAULT_US * (long long)c->clock_khz / 1000);
         SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync + 28, 0, sizeof(uint32_t), c->stream));
         void* args[] = {&A};
         SbProf prof(c, SB_PROF_SCORE);

@@ -185,15 +185,18 @@ def _chung_lu_args(a):
     return chung_lu(*a)
 
 
-def uneven_batch(count=4096, n_lo=50, n_hi=50000, seed=1005, workers=0):
+def uneven_batch(count=4096, n_lo=50, n_hi=50000, seed=1005, workers=0, select=None):
     """`count` Chung-Lu graphs, vertex counts log-uniform in [n_lo, n_hi],
     mean degree 8, exponent 2.5, negative fraction U(0.05, 0.30) per graph.
-    workers > 0 draws them in a spawned process pool (same graphs)."""
+    workers > 0 draws them in a spawned process pool (same graphs).
+    select (indices into the `count` graphs) yields only those graphs, each
+    exactly as the full draw gives it."""
     rng = _rng(seed)
     ns = np.floor(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), count))).astype(np.int64)
     negs = rng.uniform(0.05, 0.30, count)
     seeds = rng.integers(0, 2**62, count)
-    args = [(int(ns[i]), 8.0, 2.5, float(negs[i]), int(seeds[i])) for i in range(count)]
+    idx = range(count) if select is None else [int(i) for i in select]
+    args = [(int(ns[i]), 8.0, 2.5, float(negs[i]), int(seeds[i])) for i in idx]
     if workers > 0:
         import concurrent.futures as cf
         import multiprocessing as mp

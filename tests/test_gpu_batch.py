@@ -102,3 +102,49 @@ def test_batch_graphl_per_graph():
         oF, _ = O.graphl_round_f32(r, out[sl])
         assert np.array_equal(F_final[g], oF), g
     sb.close()
+
+
+def test_batch_of_64_benchmark_graphs_matches_per_graph_oracle():
+    """64 graphs of the benchmark's uneven batch (4096 Chung-Lu graphs with
+    50 to 50,000 vertices; the same seeded choice of 64 that the benchmark's
+    CPU baseline times), loaded as one disjoint union, 256 trees in every
+    graph: each graph's counts, state hashes and cloud equal the oracle's for
+    that graph alone (Algorithm 1).  The large graphs have split (hub) rows
+    and many BFS levels, and the scorer flushes per graph."""
+    from concurrent.futures import ThreadPoolExecutor
+    import os
+
+    import paper_2311_00869_gb300 as P
+
+    idx = np.sort(np.random.default_rng(7).choice(4096, size=64, replace=False))
+    graphs = list(synth.uneven_batch(count=4096, select=idx))
+    K = 256
+    sb = P.SignedBal(0)
+    try:
+        nv, mv = sb.load_batch(graphs)
+        sb.sample_trees(0, 0, K)
+        counts, hashes = sb.batch_frustration()
+        counts, hashes = counts.cpu().numpy(), hashes.cpu().numpy().view(np.uint64)
+        cl = sb.batch_cloud()
+    finally:
+        sb.close()
+    assert int(nv.max()) > 20000  # the shapes the case is meant to cover
+
+    def ref(gi):
+        r = O.clean_graph(*graphs[gi])
+        smp = O.sample(r, 0, 0, K)
+        return r.n, r.m, smp["counts"], smp["hashes"], O.cloud(smp["labels"], smp["counts"])
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        refs = list(ex.map(ref, range(len(graphs))))
+    for g, (rn, rm, rc, rh, rcl) in enumerate(refs):
+        assert (nv[g], mv[g]) == (rn, rm), g
+        assert np.array_equal(counts[g], rc), g
+        assert np.array_equal(hashes[g], rh), g
+        assert cl["n_states"][g] == rcl["S"].shape[0], g
+        assert cl["fr_min"][g] == rc.min(), g
+        e = cl["entries"][g]
+        assert np.array_equal(e["first_tree"], rcl["first_tree"]), g
+        assert np.array_equal(e["count"], rcl["count"]), g
+        assert np.array_equal(e["S"], rcl["S"]), g
+        assert np.array_equal(e["hash"], rcl["H"]), g

@@ -47,6 +47,29 @@ def test_static_forward_matches_context_forward():
             assert torch.equal(F, ref_F)
             diff = (loss.double() - ref_loss.double()).abs().cpu().numpy()
             assert np.all(diff <= bound)
+    # it allocates nothing: free device memory is the same before and after
+    # repeated calls (the first call above has done the one-time set-up)
+    R = 256
+    gam = torch.from_numpy(synth.gamma0(n1, R, seed=3)).cuda()
+    loss = torch.empty(R, device="cuda")
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _call in range(5):
+        assert lib.sb_graphL_fwd_static(ctypes.c_void_p(packed.data_ptr()), m1, ctypes.c_void_p(gam.data_ptr()), R,
+                                        ctypes.c_void_p(loss.data_ptr()), None, stream) == 0  # F_out may be null
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    ref_loss, _ = sb.graphL_fwd(gam)
+    assert np.all((loss.double() - ref_loss.double()).abs().cpu().numpy() <= 1e-5 * 0.5 * (1.0 + (
+        gam[eu.long()].double() * gam[ev.long()].double()).abs()).sum(dim=0).cpu().numpy())
+    # no edges: every loss and every discrete loss is 0
+    loss0 = torch.full((R,), float("nan"), device="cuda")
+    F0 = torch.full((R,), -1, dtype=torch.int32, device="cuda")
+    assert lib.sb_graphL_fwd_static(None, 0, ctypes.c_void_p(gam.data_ptr()), R, ctypes.c_void_p(loss0.data_ptr()),
+                                    ctypes.c_void_p(F0.data_ptr()), stream) == 0
+    torch.cuda.synchronize()
+    assert torch.all(loss0 == 0) and torch.all(F0 == 0)
     # sizes beyond the stated maximum are refused before anything runs
     big = torch.zeros((4, 2048), device="cuda")
     out = torch.zeros(2048, device="cuda")
