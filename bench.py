@@ -396,6 +396,7 @@ def main():
     }
     line["roofline"] = roofline(prof, n1, m1, K, r["stats"], peak_hps)
     extras["roofline_score"] = roofline_family("score", prof, n1, m1, K)
+    extras["roofline_hash"] = roofline_family("hash", prof, n1, m1, K)
     if not args.no_extras and rank == 0:
         try:
             line["e2e"] = e2e_leg(P, sb, n, u, v, s, K)
@@ -552,7 +553,7 @@ def roofline_family(fam, prof, n, m, K, stats=None, peak_hps=None):
     if per_launch is None:
         return None
     achieved = per_launch / avg_s / 1e9
-    return {"bound": "hbm", "kernel": {"score": "k_score", "hash": "k_state_hash", "cloud": "cloud"}[fam],
+    return {"bound": "hbm", "kernel": {"score": "k_score", "hash": "k_state_hash_tab", "cloud": "cloud"}[fam],
             "achieved": achieved, "peak": hbm, "peak_source": src, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": NCU_TRAFFIC_BYTES.get(fam), "algorithmic_bytes_per_launch": per_launch,
             "avg_launch_ms": 1000 * avg_s, "launches": launches}
@@ -725,7 +726,10 @@ def batch_leg(args, P):
     """Uneven batch: `--graphs` Chung-Lu graphs (vertex counts log-uniform in
     [50, 50000], mean degree 8, exponent 2.5, 5-30% negative), 256 trees per
     graph in one sampling call over the disjoint union, per-graph clouds, and
-    32 graphL start points per graph for `--steps` descent steps."""
+    32 graphL start points per graph for `--steps` descent steps.  The steps
+    are timed three ways: one call per stage with its host synchronisation,
+    sb_batch_steps with the kernels enqueued directly, and sb_batch_steps
+    replaying one captured CUDA graph per step."""
     import torch
 
     import synth
@@ -756,6 +760,20 @@ def batch_leg(args, P):
     ms = ev0.elapsed_time(ev1) / args.steps
     prof = sb.profile_read()
     bfs_stats = sb.stats()
+    # the same steps with no host synchronisation: kernels enqueued directly,
+    # and one step captured as a CUDA graph and replayed
+    steps_ms = {}
+    fr_steps = {}
+    for use_graph in (False, True):
+        sb.batch_steps(SEED, 0, K, 2, use_graph=use_graph)  # warm-up (and capture)
+        sb.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fr, _ = sb.batch_steps(SEED, args.warmup * K, K, args.steps, use_graph=use_graph)
+        e1.record()
+        sb.sync()
+        steps_ms["graph" if use_graph else "direct"] = e0.elapsed_time(e1) / args.steps
+        fr_steps[use_graph] = fr.cpu().numpy()
     g0 = torch.from_numpy(synth.gamma0(n_tot, R, seed=0)).cuda()
     out = torch.empty_like(g0)
     steps_gl = 100
@@ -774,6 +792,9 @@ def batch_leg(args, P):
         "config": {"workload": f"uneven_batch_{args.graphs}_chung_lu", "graphs": args.graphs, "n_total": n_tot,
                    "m_total": m_tot, "trees_per_graph": K, "graphl_R": R, "generation_s": gen_s},
         "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
+        "steps_no_sync_ms": steps_ms,
+        "steps_no_sync_edge_evals_per_s": {k: K * m_tot / (v / 1000.0) for k, v in steps_ms.items()},
+        "steps_graph_equals_direct": bool(np.array_equal(fr_steps[False], fr_steps[True])),
         "graphl_steps_per_s": steps_gl / (gl_ms / 1000.0),
         "fr_min_median": float(np.median(cl["fr_min"])),
         "states_median": float(np.median(cl["n_states"])),

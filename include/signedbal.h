@@ -77,7 +77,8 @@ const char* sb_last_error(const sb_ctx* ctx);
 /* Replaces cudaMalloc/cudaFree for context-owned buffers (e.g. with a
    framework's caching allocator).  Call before sb_load_graph. */
 sb_status sb_set_allocator(sb_ctx* ctx, sb_alloc_fn alloc, sb_free_fn free_fn, void* user);
-/* Waits for the stream and reports any pending device error. */
+/* Waits for the stream and reports any pending device error, including a
+   device wait that ran out during sb_batch_steps (SB_ERR_TIMEOUT). */
 sb_status sb_sync(sb_ctx* ctx);
 
 /* Kernel families timed by the profiler (sb_profile / sb_profile_read). */
@@ -103,8 +104,9 @@ sb_status sb_profile_read(sb_ctx* ctx, double* ms_out, int64_t* launches_out);
 /* Run-time tuning knobs (chosen by the package's autotuner; 0 = default):
    SB_TUNE_BFS_WORDS         64-tree words grown per BFS launch (1..32; 32)
    SB_TUNE_SCORE_BLOCKS_SM   scorer blocks per SM (0 = as many as fit)
-   SB_TUNE_GL_LANES          graphL lanes per row segment: 8 (32 columns)
-                             or 32 (128 columns) when R % 4 == 0 (8)
+   SB_TUNE_GL_LANES          graphL lanes per row segment: 8 (32 columns),
+                             16 (64 columns) or 32 (128 columns) when
+                             R % 4 == 0 (8)
    SB_TUNE_BFS_GROUP         lanes that share one vertex in the BFS, a power
                              of two in [1, 32]; used when it is at most twice
                              the launch's words rounded up to a power of two
@@ -214,6 +216,28 @@ sb_status sb_load_batch(sb_ctx* ctx, int64_t n_graphs, const int64_t* nv, const 
  * in order of first appearance.
  */
 sb_status sb_batch_cloud(sb_ctx* ctx, int32_t* n_states_out, int32_t* fr_min_out, sb_cloud_entry* entries_out);
+
+/*
+ * `steps` graphBpp steps on the loaded batch of graphs (Algorithm 1 on every
+ * graph at once) with no host synchronisation: step i samples the BFS trees
+ * [tree_begin + i K, tree_begin + (i + 1) K) in every graph, counts and
+ * hashes their states and builds each graph's cloud of the step's trees,
+ * exactly as sb_sample_trees, sb_frustration and sb_batch_cloud do.
+ * use_graph = 1 runs the first step directly, captures the second into a CUDA
+ * graph (once; it is replayed while seed, K, the batch and the tuning stay the
+ * same) and replays it for the remaining steps; the device holds the first
+ * tree of the current step and every replay moves it on by K.  use_graph = 0
+ * enqueues every step's kernels directly.  The results are the same.
+ * Outputs (device, G entries, nullable): fr_min_out[g] = the smallest S of
+ * graph g over all the steps' trees; n_states_out[g] = the distinct states of
+ * graph g in the last step.  The call only enqueues work on the context's
+ * stream: the outputs are ready, and a device wait that ran out during the
+ * steps is reported (SB_ERR_TIMEOUT), by sb_sync.  Afterwards sb_label,
+ * sb_frustration and sb_batch_cloud see the last step's trees.
+ * K in [1, 1024], steps >= 1; SB_ERR_STATE without a batch of graphs.
+ */
+sb_status sb_batch_steps(sb_ctx* ctx, uint64_t seed, int64_t tree_begin, int64_t K, int32_t steps, int32_t use_graph,
+                         int32_t* fr_min_out, int32_t* n_states_out);
 
 /* ---------------------------------------------------------------- graphBpp */
 

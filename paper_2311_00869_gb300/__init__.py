@@ -151,6 +151,19 @@ class SignedBal:
                               for g in range(G)]
         return out
 
+    def batch_steps(self, seed, tree_begin, K, steps, use_graph=True, fr_min=None, n_states=None):
+        """`steps` graphBpp steps over the batch without host synchronisation
+        (one step captured into a CUDA graph and replayed when use_graph);
+        returns the device tensors (fr_min over all steps, n_states of the
+        last step), G entries each, valid after sync()."""
+        G = self.batch_G
+        fr_min = torch.empty(G, dtype=torch.int32, device=self.device) if fr_min is None else fr_min
+        n_states = torch.empty(G, dtype=torch.int32, device=self.device) if n_states is None else n_states
+        self._check(self.lib.sb_batch_steps(self.h, seed, tree_begin, K, steps, 1 if use_graph else 0, _ptr(fr_min),
+                                            _ptr(n_states)))
+        self.K = K
+        return fr_min, n_states
+
     def graph_edges(self):
         u = torch.empty(self.m, dtype=torch.int32, device=self.device)
         v = torch.empty_like(u)

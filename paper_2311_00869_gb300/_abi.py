@@ -33,6 +33,7 @@ SIGNATURES = {
     "sb_load_graph": (i32, [P, i64, i64, P, P, P, u32, ctypes.POINTER(i64), ctypes.POINTER(i64), P]),
     "sb_load_batch": (i32, [P, i64, P, P, P, P, P, u32, P, P]),
     "sb_batch_cloud": (i32, [P, P, P, P]),
+    "sb_batch_steps": (i32, [P, u64, i64, i64, i32, i32, P, P]),
     "sb_graph_edges": (i32, [P, P, P, P]),
     "sb_graph_csr": (i32, [P, P, P, P]),
     "sb_sample_trees": (i32, [P, u64, i64, i64, P]),

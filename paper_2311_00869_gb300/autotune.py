@@ -5,7 +5,7 @@ CUDA-event profiler and keeps the fastest per knob:
   bfs_words        64-tree words grown per BFS launch (trees per launch / 64)
   bfs_group        lanes sharing one vertex in the BFS (the words, or twice that)
   score_blocks_sm  blocks per SM of the frustration scorer
-  gl_lanes         graphL lanes per row segment (8 -> 32 columns, 32 -> 128)
+  gl_lanes         graphL lanes per row segment (8 -> 32 columns, 16 -> 64, 32 -> 128)
 Choices are cached in JSON per (GPU name, graph shape bucket, K, R), so a
 later run on the same kind of graph skips the timing.  Results never depend on
 the knobs; only speed does.
@@ -114,7 +114,7 @@ def tune(sb, K: int = 1024, R: int | None = None, seed: int = 987654321, reps: i
         g0 = (torch.rand((sb.n, R), generator=gen) * 2 - 1).to(sb.device)
         grad_out = torch.ones(sb._per_graph() * R, device=sb.device)  # G x R in a batch
         best = None
-        for lanes in ((8, 32) if R % 4 == 0 else (8,)):
+        for lanes in ((8, 16, 32) if R % 4 == 0 else (8,)):
             sb.set_tuning(gl_lanes=lanes)
             t = _time_family(sb, "gl_rows", lambda: sb.graphL_bwd(g0, grad_out), reps)
             if best is None or t < best[0]:

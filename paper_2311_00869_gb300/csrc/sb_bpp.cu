@@ -21,7 +21,7 @@
 #define BFS_THREADS 128
 #define BFS_THREADS_PAR 128
 #define BFS_QUEUE_PER_LANE 32  // candidate-queue entries per lane (overflow falls back to per-lane hashing)
-#define SYNC_WORDS 32
+#define SYNC_WORDS 48
 // Shared-memory slots of (owner thread o, tree t): owner-major rows padded so
 // that one owner's trees, and one tree of consecutive owners, fall in
 // different banks (the hash rounds walk one owner's trees in lockstep).
@@ -47,7 +47,7 @@ struct BfsArgs {
     int32_t* parents;   // K x n or null
     int64_t n;
     uint64_t S;         // seed key
-    int64_t tree0;      // global index of batch tree 0
+    const int64_t* tree0;  // global index of batch tree 0 (device)
     const int32_t* vgoff;  // first vertex of each vertex's graph (batches), or null
     long long wait;        // SM cycles a barrier wait may take before it reports a timeout
     unsigned bar_extra;    // arrivals a barrier expects beyond the launch's blocks (0; 1 tests the timeout path)
@@ -338,8 +338,9 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
     const int64_t group_id = (int64_t)blockIdx.x * (BD / G) + tid / G;
     const unsigned nblocks = gridDim.x + A.bar_extra;
 
+    const int64_t tree0 = *A.tree0;
     for (int i = tid; i < A.Wb * 64; i += BD)
-        akey[KSLOT(i >> 6, i & 63)] = (uint32_t)sb_tree_key(A.S, A.tree0 + 64 * (int64_t)A.w0 + i);
+        akey[KSLOT(i >> 6, i & 63)] = (uint32_t)sb_tree_key(A.S, tree0 + 64 * (int64_t)A.w0 + i);
     if (tid == 0) s_any = 0;
     __syncthreads();
 
@@ -528,9 +529,10 @@ __global__ void k_hub_init(int64_t nh, int Wb, uint64_t* hubnew, uint64_t* hubbe
 }
 
 // root of every tree of this launch in every graph (one graph unless voff)
-__global__ void k_bfs_roots(int64_t n, int Wb, int w0, int64_t K, uint64_t S, int64_t tree0, uint64_t* vis,
+__global__ void k_bfs_roots(int64_t n, int Wb, int w0, int64_t K, uint64_t S, const int64_t* tree0p, uint64_t* vis,
                             uint64_t* fr0, int32_t* parents, const int32_t* voff, int64_t G)
 {
+    const int64_t tree0 = *tree0p;
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t per = 64 * (int64_t)Wb;
     if (x >= per * G) return;
@@ -559,64 +561,117 @@ __global__ void k_flip(const uint64_t* lab, int W, uint64_t* flipw, const int32_
     flipw[x] = lab[(voff ? (int64_t)voff[g] : 0) * W + w];
 }
 
-// H_t = sum of weights of vertices whose canonical label is 1 (mod 2^64),
-// per graph.  Block: 64 lanes per word bit x 4 vertex strides; grid.y = word.
-// Sums are flushed with integer atomics (order-free) when the graph changes.
-#define HASH_VCHUNK 2048
-__global__ void __launch_bounds__(256) k_state_hash(const uint64_t* __restrict__ lab, int64_t n, int W,
-                                                    const uint64_t* __restrict__ flipw,
-                                                    const uint64_t* __restrict__ weight,
-                                                    const int32_t* __restrict__ vgid, int64_t KP,
-                                                    unsigned long long* __restrict__ H)
+// The same state hashes from subset-sum tables.  A block takes a contiguous
+// range of 32-vertex groups.  For each group it tabulates, for each of the
+// group's four runs of 8 vertices, the 256 subset sums of their weights; a
+// warp then takes one 64-tree word at a time: lane k loads vertex k's label
+// word, two 32 x 32 bit transposes across the warp give lane j the group's
+// vertices labelled 1 in trees j and j + 32, and four table lookups per tree
+// add their weights.  The sums are over raw labels (root labelled 0): the
+// canonical flip of a tree is applied afterwards (k_state_hash_flip), as
+// H = W_g - H_raw when the tree's vertex 0 is labelled 1, W_g = total weight
+// of graph g (Sec. 2: the canonical state is the raw one switched at every
+// vertex, so its 1-set is the complement).  A group with vertices of several
+// graphs (batches) is taken once per graph, with the other graphs' weights
+// left out of the tables.
+#define HT_THREADS 256
+#define HT_WARPS (HT_THREADS / 32)
+#define HT_WPW 8  // words per warp: 64 words over 8 warps
+
+__global__ void __launch_bounds__(HT_THREADS, 4) k_state_hash_tab(const uint64_t* __restrict__ lab, int64_t n, int W,
+                                                                  const uint64_t* __restrict__ weight,
+                                                                  const int32_t* __restrict__ vgid, int64_t KP,
+                                                                  int64_t groups_per_block,
+                                                                  unsigned long long* __restrict__ Hraw,
+                                                                  unsigned long long* __restrict__ wsum)
 {
-    const int w = blockIdx.y;
-    const int b = threadIdx.x & 63, sub = threadIdx.x >> 6;
-    const int64_t v0 = (int64_t)blockIdx.x * HASH_VCHUNK;
-    const int64_t v1 = min(n, v0 + HASH_VCHUNK);
-    int64_t gcur = vgid ? vgid[min(v0 + sub, n - 1)] : 0;
-    uint64_t fl = flipw[gcur * W + w], acc = 0;
-    int64_t v = v0 + sub;
-    // 8 vertices (stride 4) per round: their label words and weights are
-    // loaded before any is added
-    for (; v + 28 < v1; v += 32) {
-        uint64_t x[8], wt[8];
+    // double-buffered, so that the tables of one group are built while no
+    // thread can still be reading the buffer from two groups before
+    __shared__ uint64_t tab[2][4][256];
+    __shared__ uint64_t sw[2][32];
+    const unsigned lane = threadIdx.x & 31u;
+    const int warp = (int)(threadIdx.x >> 5);
+    const int64_t ngroups = sb_cdiv(n, 32);
+    const int64_t q0 = (int64_t)blockIdx.x * groups_per_block;
+    const int64_t q1 = min(ngroups, q0 + groups_per_block);
+    uint64_t accA[HT_WPW], accB[HT_WPW];
 #pragma unroll
-        for (int i = 0; i < 8; i++) {
-            x[i] = lab[(v + 4 * i) * W + w];
-            wt[i] = weight[v + 4 * i];
-        }
-        bool same = true;
-        if (vgid) {
+    for (int i = 0; i < HT_WPW; i++) accA[i] = accB[i] = 0;
+    int64_t gcur = -1;
+    int buf = 0;
+    auto flush = [&]() {
+        if (gcur < 0) return;
 #pragma unroll
-            for (int i = 0; i < 8; i++) same = same && vgid[v + 4 * i] == gcur;
-        }
-        if (same) {
-#pragma unroll
-            for (int i = 0; i < 8; i++) acc += (((x[i] ^ fl) >> b) & 1ull) ? wt[i] : 0ull;
-        } else {
-            for (int i = 0; i < 8; i++) {
-                const int64_t g = vgid[v + 4 * i];
-                if (g != gcur) {
-                    if (acc) atomicAdd(H + gcur * KP + 64 * w + b, (unsigned long long)acc);
-                    acc = 0;
-                    gcur = g;
-                    fl = flipw[g * W + w];
-                }
-                acc += (((x[i] ^ fl) >> b) & 1ull) ? wt[i] : 0ull;
+        for (int i = 0; i < HT_WPW; i++) {
+            const int w = warp + HT_WARPS * i;
+            if (w < W) {
+                if (accA[i]) atomicAdd(Hraw + gcur * KP + 64 * w + lane, (unsigned long long)accA[i]);
+                if (accB[i]) atomicAdd(Hraw + gcur * KP + 64 * w + 32 + lane, (unsigned long long)accB[i]);
             }
+            accA[i] = accB[i] = 0;
+        }
+    };
+    // table b, subsets s0 .. s0 + 3 of vertices 8 b .. 8 b + 7 of the group
+    const int tb = (int)(threadIdx.x >> 6), s0 = (int)(threadIdx.x & 63u) << 2;
+    for (int64_t q = q0; q < q1; q++) {
+        const int64_t v0 = q * 32;
+        const int64_t vk = v0 + lane;
+        const int64_t vlast = min(n, v0 + 32) - 1;
+        const int64_t ga = vgid ? vgid[v0] : 0, gb = vgid ? vgid[vlast] : 0;
+        for (int64_t g = ga; g <= gb; g++) {  // the graphs present in the group (almost always one)
+            if (g != gcur) {
+                flush();
+                gcur = g;
+            }
+            if (warp == 0) {  // the group's weights, and its share of the graph's total weight
+                const uint64_t x = (vk < n && (!vgid || vgid[vk] == g)) ? weight[vk] : 0ull;
+                sw[buf][lane] = x;
+                uint64_t t = x;
+#pragma unroll
+                for (int dd = 16; dd; dd >>= 1) t += __shfl_xor_sync(0xffffffffu, t, dd);
+                if (lane == 0 && t) atomicAdd(wsum + g, (unsigned long long)t);
+            }
+            __syncthreads();
+            {
+                const uint64_t* w8 = sw[buf] + 8 * tb;
+                uint64_t base = 0;
+#pragma unroll
+                for (int i = 2; i < 8; i++)
+                    if ((s0 >> i) & 1) base += w8[i];
+                uint64_t* t4 = tab[buf][tb] + s0;
+                t4[0] = base;
+                t4[1] = base + w8[0];
+                t4[2] = base + w8[1];
+                t4[3] = base + w8[0] + w8[1];
+            }
+            __syncthreads();
+            const uint64_t(*T)[256] = tab[buf];
+#pragma unroll
+            for (int i = 0; i < HT_WPW; i++) {
+                const int w = warp + HT_WARPS * i;
+                if (w >= W) break;
+                const uint64_t L = vk < n ? lab[vk * W + w] : 0ull;
+                const uint32_t MA = warp_transpose32((uint32_t)L, lane);
+                const uint32_t MB = warp_transpose32((uint32_t)(L >> 32), lane);
+                accA[i] += T[0][MA & 255u] + T[1][(MA >> 8) & 255u] + T[2][(MA >> 16) & 255u] + T[3][MA >> 24];
+                accB[i] += T[0][MB & 255u] + T[1][(MB >> 8) & 255u] + T[2][(MB >> 16) & 255u] + T[3][MB >> 24];
+            }
+            buf ^= 1;
         }
     }
-    for (; v < v1; v += 4) {
-        const int64_t g = vgid ? vgid[v] : 0;
-        if (g != gcur) {
-            if (acc) atomicAdd(H + gcur * KP + 64 * w + b, (unsigned long long)acc);
-            acc = 0;
-            gcur = g;
-            fl = flipw[g * W + w];
-        }
-        acc += (((lab[v * W + w] ^ fl) >> b) & 1ull) ? weight[v] : 0ull;
-    }
-    if (acc) atomicAdd(H + gcur * KP + 64 * w + b, (unsigned long long)acc);
+    flush();
+}
+
+// canonical flip of the raw sums: trees whose vertex 0 (of the tree's graph)
+// is labelled 1 take the complement's weight
+__global__ void k_state_hash_flip(unsigned long long* H, const unsigned long long* wsum, const uint64_t* flipw, int W,
+                                  int64_t KP, int64_t G)
+{
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= KP * G) return;
+    const int64_t g = x / KP;
+    const int64_t t = x - g * KP;
+    if ((flipw[g * W + t / 64] >> (t % 64)) & 1ull) H[x] = wsum[g] - H[x];
 }
 
 __global__ void k_canon_out(const uint64_t* __restrict__ lab, int64_t total, int W, int64_t K,
@@ -670,6 +725,7 @@ static sb_status ensure_sync(sb_ctx* c)
     if (!c->sync) {
         c->sync = (uint32_t*)sb_dalloc(c, sizeof(uint32_t) * SYNC_WORDS);
         if (!c->sync) return sb_fail(c, SB_ERR_OOM, "sync words");
+        SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync, 0, sizeof(uint32_t) * SYNC_WORDS, c->stream));
     }
     return SB_OK;
 }
@@ -700,10 +756,13 @@ static sb_status run_bfs(sb_ctx* c, int w0, int Wb, int32_t* parents)
     }
     const int64_t ngraphs = c->batch_G > 0 ? c->batch_G : 1;
     k_bfs_roots<<<(unsigned)sb_cdiv(64 * Wb * ngraphs, 256), 256, 0, c->stream>>>(
-        n, Wb, w0, c->K, sb_seed_key(c->seed), c->tree_begin, c->vis, c->fr0, parents,
+        n, Wb, w0, c->K, sb_seed_key(c->seed), sb_tree0_ptr(c->sync), c->vis, c->fr0, parents,
         c->batch_G > 0 ? c->b_voff : nullptr, ngraphs);
     SB_TRY(sb_after_launch(c, "k_bfs_roots"));
-    SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync, 0, sizeof(uint32_t) * 16, c->stream));
+    // level counters and barrier words of this launch (the error word sync[6]
+    // is cleared per batch, so that an error of an earlier launch stays)
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync, 0, sizeof(uint32_t) * 6, c->stream));
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync + 7, 0, sizeof(uint32_t) * 9, c->stream));
     BfsArgs A;
     A.items = c->items;
     A.n_items = c->n_items;
@@ -724,18 +783,61 @@ static sb_status run_bfs(sb_ctx* c, int w0, int Wb, int32_t* parents)
     A.parents = parents;
     A.n = n;
     A.S = sb_seed_key(c->seed);
-    A.tree0 = c->tree_begin;
+    A.tree0 = sb_tree0_ptr(c->sync);
     A.vgoff = c->batch_G > 0 ? c->vgoff : nullptr;
     A.wait = sb_wait_cycles(c);
     A.bar_extra = c->tune[SB_TUNE_STALL_TEST] ? 1u : 0u;
     void* args[] = {&A};
     {
+        // a cooperative launch (every block resident for the grid barrier),
+        // issued through the launch-attribute form so that it can also be
+        // captured into a CUDA graph
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeCooperative;
+        attr.val.cooperative = 1;
+        cfg.gridDim = dim3(nblocks);
+        cfg.blockDim = dim3(BD);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = c->stream;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
         SbProf prof(c, SB_PROF_BFS);
-        SB_CHECK_CUDA(c, cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(BD), args, smem, c->stream));
+        SB_CHECK_CUDA(c, cudaLaunchKernelExC(&cfg, fn, args));
         SB_TRY(sb_after_launch(c, "k_bfs"));
     }
     k_fold_stats<<<1, 1, 0, c->stream>>>(c->sync, (unsigned long long*)(c->sync + 16));
     return sb_after_launch(c, "k_fold_stats");
+}
+
+// *p = v, or *p += add when add != 0 (the device copy of the first tree)
+__global__ void k_set_i64(int64_t* p, int64_t v, int64_t add)
+{
+    if (add) *p += add;
+    else *p = v;
+}
+
+// errors of one step kept across the steps of sb_batch_steps: BFS barrier
+// (sync[6]) and scorer tile copies (sync[28]) into sync[34]
+__global__ void k_latch_errors(uint32_t* sync)
+{
+    uint32_t e = 0;
+    if (sync[6] & 1u) e |= 1u;
+    if (sync[6] & ~1u) e |= 2u;
+    if (sync[28]) e |= 1u;
+    if (e) atomicOr(sync + 34, e);
+}
+
+__global__ void k_fold_min(int32_t* acc, const int32_t* x, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc[i] = min(acc[i], x[i]);
+}
+
+__global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
 }
 
 static sb_status check_sync_error(sb_ctx* c)
@@ -760,15 +862,13 @@ sb_status sb_batch_begin(sb_ctx* c, uint64_t seed, int64_t tree_begin, int64_t K
         c->labels = (uint64_t*)sb_dalloc(c, lab_bytes);
         c->labels_cap = c->labels ? lab_bytes : 0;
     }
-    sb_dfree(c, c->flipw);
-    sb_dfree(c, c->hashes);
-    sb_dfree(c, c->counts);
     const int64_t G = c->batch_G > 0 ? c->batch_G : 1;  // per-graph results in a batch
-    c->flipw = (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * W * G);
-    c->hashes = (uint64_t*)sb_dalloc(c, sizeof(uint64_t) * 64 * W * G);
-    c->counts = (int32_t*)sb_dalloc(c, sizeof(int32_t) * 64 * W * G);
+    // kept while large enough, so that repeated calls allocate nothing
+    sb_status st = sb_ensure(c, (void**)&c->flipw, &c->flipw_cap, sizeof(uint64_t) * W * G);
+    if (st == SB_OK) st = sb_ensure(c, (void**)&c->hashes, &c->hashes_cap, sizeof(uint64_t) * 64 * W * G);
+    if (st == SB_OK) st = sb_ensure(c, (void**)&c->counts, &c->counts_cap, sizeof(int32_t) * 64 * W * G);
     c->has_batch = false;
-    if (!c->labels || !c->flipw || !c->hashes || !c->counts)
+    if (st != SB_OK || !c->labels || !c->flipw || !c->hashes || !c->counts)
         return sb_fail(c, SB_ERR_OOM, "batch storage (n=%lld, K=%lld)", (long long)n, (long long)K);
     c->seed = seed;
     c->tree_begin = tree_begin;
@@ -777,7 +877,9 @@ sb_status sb_batch_begin(sb_ctx* c, uint64_t seed, int64_t tree_begin, int64_t K
     c->counts_valid = false;
     c->batch_in_cloud = false;
     SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync + 16, 0, sizeof(uint32_t) * 16, c->stream));
-    return SB_OK;
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync + 6, 0, sizeof(uint32_t), c->stream));
+    k_set_i64<<<1, 1, 0, c->stream>>>(sb_tree0_ptr(c->sync), tree_begin, 0);
+    return sb_after_launch(c, "k_set_i64");
 }
 
 sb_status sb_batch_end(sb_ctx* c)
@@ -788,31 +890,36 @@ sb_status sb_batch_end(sb_ctx* c)
                                                                           c->batch_G > 0 ? c->b_voff : nullptr, G);
     SB_TRY(sb_after_launch(c, "k_flip"));
     SB_CHECK_CUDA(c, cudaMemsetAsync(c->hashes, 0, sizeof(uint64_t) * 64 * W * G, c->stream));
+    SB_TRY(sb_ensure(c, (void**)&c->hwsum, &c->hwsum_cap, sizeof(uint64_t) * (size_t)G));
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->hwsum, 0, sizeof(uint64_t) * (size_t)G, c->stream));
     {
         SbProf prof(c, SB_PROF_HASH);
-        dim3 hg((unsigned)sb_cdiv(n, HASH_VCHUNK), (unsigned)W);
-        k_state_hash<<<hg, 256, 0, c->stream>>>(c->labels, n, W, c->flipw, c->vweight,
-                                                c->batch_G > 0 ? c->vgid : nullptr, 64 * (int64_t)W,
-                                                (unsigned long long*)c->hashes);
-        SB_TRY(sb_after_launch(c, "k_state_hash"));
+        const int64_t ngroups = sb_cdiv(n, 32);
+        const int64_t nblk = std::max<int64_t>(1, std::min<int64_t>((int64_t)c->num_sms * 4, sb_cdiv(ngroups, 16)));
+        const int64_t per = sb_cdiv(ngroups, nblk);
+        k_state_hash_tab<<<(unsigned)sb_cdiv(ngroups, per), HT_THREADS, 0, c->stream>>>(
+            c->labels, n, W, c->vweight, c->batch_G > 0 ? c->vgid : nullptr, 64 * (int64_t)W, per,
+            (unsigned long long*)c->hashes, (unsigned long long*)c->hwsum);
+        SB_TRY(sb_after_launch(c, "k_state_hash_tab"));
+        k_state_hash_flip<<<(unsigned)sb_cdiv(64 * (int64_t)W * G, 256), 256, 0, c->stream>>>(
+            (unsigned long long*)c->hashes, (const unsigned long long*)c->hwsum, c->flipw, W, 64 * (int64_t)W, G);
+        SB_TRY(sb_after_launch(c, "k_state_hash_flip"));
     }
     c->has_batch = true;
     return SB_OK;
 }
 
-extern "C" sb_status sb_sample_trees(sb_ctx* c, uint64_t seed, int64_t tree_begin, int64_t K, int32_t* parents_out)
+static int bfs_words_per_launch(const sb_ctx* c)
 {
-    if (!c) return SB_ERR_ARG;
-    if (!c->has_graph) return sb_fail(c, SB_ERR_STATE, "no graph loaded");
-    if (K < 1 || K > SB_TREES_MAX || tree_begin < 0)
-        return sb_fail(c, SB_ERR_ARG, "K must be in [1, %d] and tree_begin >= 0", SB_TREES_MAX);
-    if (parents_out && !sb_is_device_ptr(parents_out))
-        return sb_fail(c, SB_ERR_ARG, "parents_out must be a device pointer");
-    SB_CHECK_CUDA(c, cudaSetDevice(c->device));
-    SB_TRY(sb_batch_begin(c, seed, tree_begin, K));
+    return c->tune[SB_TUNE_BFS_WORDS] > 0 ? (int)c->tune[SB_TUNE_BFS_WORDS] : SB_WORDS_MAX;
+}
+
+// BFS scratch for the current batch (kept while large enough)
+static sb_status bfs_alloc(sb_ctx* c)
+{
     const int64_t n = c->n;
     const int W = c->W;
-    const int WL = c->tune[SB_TUNE_BFS_WORDS] > 0 ? (int)c->tune[SB_TUNE_BFS_WORDS] : SB_WORDS_MAX;  // words per launch
+    const int WL = bfs_words_per_launch(c);
     const int Wb_max = W < WL ? W : WL;
     size_t words = (size_t)n * Wb_max;
     if (c->bfs_cap_words < words) {
@@ -831,15 +938,154 @@ extern "C" sb_status sb_sample_trees(sb_ctx* c, uint64_t seed, int64_t tree_begi
     }
     if (!c->done) c->done = (int32_t*)sb_dalloc(c, sizeof(int32_t) * (size_t)n);
     if (!c->bfs_cap_words || !c->done)
-        return sb_fail(c, SB_ERR_OOM, "BFS batch storage (n=%lld, K=%lld)", (long long)n, (long long)K);
-    sb_status st = SB_OK;
-    for (int w0 = 0; w0 < W && st == SB_OK; w0 += WL) {
-        int Wb = W - w0 < WL ? W - w0 : WL;
-        st = run_bfs(c, w0, Wb, parents_out);
+        return sb_fail(c, SB_ERR_OOM, "BFS batch storage (n=%lld, K=%lld)", (long long)n, (long long)c->K);
+    return SB_OK;
+}
+
+// the BFS launches of the current batch (no host synchronisation)
+static sb_status bfs_enqueue(sb_ctx* c, int32_t* parents_out)
+{
+    const int W = c->W, WL = bfs_words_per_launch(c);
+    for (int w0 = 0; w0 < W; w0 += WL) {
+        const int Wb = W - w0 < WL ? W - w0 : WL;
+        SB_TRY(run_bfs(c, w0, Wb, parents_out));
     }
+    return SB_OK;
+}
+
+extern "C" sb_status sb_sample_trees(sb_ctx* c, uint64_t seed, int64_t tree_begin, int64_t K, int32_t* parents_out)
+{
+    if (!c) return SB_ERR_ARG;
+    if (!c->has_graph) return sb_fail(c, SB_ERR_STATE, "no graph loaded");
+    if (K < 1 || K > SB_TREES_MAX || tree_begin < 0)
+        return sb_fail(c, SB_ERR_ARG, "K must be in [1, %d] and tree_begin >= 0", SB_TREES_MAX);
+    if (parents_out && !sb_is_device_ptr(parents_out))
+        return sb_fail(c, SB_ERR_ARG, "parents_out must be a device pointer");
+    SB_CHECK_CUDA(c, cudaSetDevice(c->device));
+    SB_TRY(sb_batch_begin(c, seed, tree_begin, K));
+    SB_TRY(bfs_alloc(c));
+    const sb_status st = bfs_enqueue(c, parents_out);
     c->tune[SB_TUNE_STALL_TEST] = 0;  // a test of the timeout path covers one call
     SB_TRY(st);
     return sb_batch_end(c);
+}
+
+// One step of sb_batch_steps for the batch set up by sb_batch_begin: trees
+// of the device's current range, counts, hashes and per-graph clouds, then
+// the range moves on by K.  Enqueue only: no allocation, no host
+// synchronisation, so that the step can be captured into a CUDA graph.
+static sb_status batch_step_enqueue(sb_ctx* c)
+{
+    const int64_t G = c->batch_G;
+    SB_TRY(bfs_enqueue(c, nullptr));
+    SB_TRY(sb_batch_end(c));
+    SB_TRY(sb_score_enqueue(c));
+    k_latch_errors<<<1, 1, 0, c->stream>>>(c->sync);
+    SB_TRY(sb_after_launch(c, "k_latch_errors"));
+    SB_TRY(sb_batch_cloud_enqueue(c, c->bs_ns, c->bs_fm));
+    k_fold_min<<<(unsigned)sb_cdiv(G, 256), 256, 0, c->stream>>>(c->bs_frmin, c->bs_fm, G);
+    SB_TRY(sb_after_launch(c, "k_fold_min"));
+    k_set_i64<<<1, 1, 0, c->stream>>>(sb_tree0_ptr(c->sync), 0, c->K);
+    return sb_after_launch(c, "k_set_i64");
+}
+
+// Captures one step into a CUDA graph (or reuses the captured one while its
+// key matches) and launches it `reps` times on c->stream.
+static sb_status batch_steps_graph(sb_ctx* c, const uint64_t* key, int reps)
+{
+    if (!(c->bs_exec && memcmp(key, c->bs_exec_key, sizeof(c->bs_exec_key)) == 0)) {
+        if (c->bs_exec) cudaGraphExecDestroy(c->bs_exec);
+        c->bs_exec = nullptr;
+        cudaGraph_t graph = nullptr;
+        SB_CHECK_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+        c->capturing = true;
+        const sb_status st = batch_step_enqueue(c);
+        c->capturing = false;
+        const cudaError_t ec = cudaStreamEndCapture(c->stream, &graph);
+        if (st != SB_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (ec != cudaSuccess) return sb_cuda_fail(c, ec, "cudaStreamEndCapture");
+        const cudaError_t ei = cudaGraphInstantiate(&c->bs_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            c->bs_exec = nullptr;
+            return sb_cuda_fail(c, ei, "cudaGraphInstantiate");
+        }
+        memcpy(c->bs_exec_key, key, sizeof(c->bs_exec_key));
+    }
+    for (int r = 0; r < reps; r++) {
+        SbProf prof(c, SB_PROF_BFS);  // a replay is timed as one step (the BFS dominates it)
+        SB_CHECK_CUDA(c, cudaGraphLaunch(c->bs_exec, c->stream));
+    }
+    return SB_OK;
+}
+
+extern "C" sb_status sb_batch_steps(sb_ctx* c, uint64_t seed, int64_t tree_begin, int64_t K, int32_t steps,
+                                    int32_t use_graph, int32_t* fr_min_out, int32_t* n_states_out)
+{
+    if (!c) return SB_ERR_ARG;
+    if (!c->has_graph || c->batch_G <= 0) return sb_fail(c, SB_ERR_STATE, "no batch of graphs loaded");
+    if (K < 1 || K > 1024 || steps < 1 || tree_begin < 0 || (use_graph != 0 && use_graph != 1))
+        return sb_fail(c, SB_ERR_ARG, "K must be in [1, 1024], steps >= 1, tree_begin >= 0, use_graph 0 or 1");
+    if ((fr_min_out && !sb_is_device_ptr(fr_min_out)) || (n_states_out && !sb_is_device_ptr(n_states_out)))
+        return sb_fail(c, SB_ERR_ARG, "fr_min_out and n_states_out must be device pointers");
+    SB_CHECK_CUDA(c, cudaSetDevice(c->device));
+    const int64_t G = c->batch_G;
+    SB_TRY(sb_batch_begin(c, seed, tree_begin, K));
+    SB_TRY(bfs_alloc(c));
+    if (c->bs_cap < (size_t)G) {
+        sb_dfree(c, c->bs_frmin);
+        sb_dfree(c, c->bs_fm);
+        sb_dfree(c, c->bs_ns);
+        c->bs_frmin = (int32_t*)sb_dalloc(c, sizeof(int32_t) * (size_t)G);
+        c->bs_fm = (int32_t*)sb_dalloc(c, sizeof(int32_t) * (size_t)G);
+        c->bs_ns = (int32_t*)sb_dalloc(c, sizeof(int32_t) * (size_t)G);
+        c->bs_cap = (c->bs_frmin && c->bs_fm && c->bs_ns) ? (size_t)G : 0;
+        if (!c->bs_cap) return sb_fail(c, SB_ERR_OOM, "batch step outputs");
+    }
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync + 34, 0, sizeof(uint32_t), c->stream));
+    k_fill_i32<<<(unsigned)sb_cdiv(G, 256), 256, 0, c->stream>>>(c->bs_frmin, G, 0x7FFFFFFF);
+    SB_TRY(sb_after_launch(c, "k_fill_i32"));
+    // the first step runs directly (it also sizes every buffer the step uses)
+    sb_status st = batch_step_enqueue(c);
+    if (st == SB_OK && steps > 1) {
+        if (use_graph) {
+            const uint64_t key[8] = {seed, (uint64_t)K, (uint64_t)G, c->graph_gen, (uint64_t)bfs_words_per_launch(c),
+                                     (uint64_t)c->tune[SB_TUNE_BFS_GROUP], (uint64_t)c->tune[SB_TUNE_SCORE_BLOCKS_SM],
+                                     (uint64_t)c->tune[SB_TUNE_WAIT_US]};
+            // capture and replay on a private stream ordered after / before
+            // the context stream (the legacy default stream cannot be captured)
+            if (!c->cap_stream) {
+                SB_CHECK_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+                SB_CHECK_CUDA(c, cudaEventCreateWithFlags(&c->cap_in, cudaEventDisableTiming));
+                SB_CHECK_CUDA(c, cudaEventCreateWithFlags(&c->cap_out, cudaEventDisableTiming));
+            }
+            cudaStream_t main_stream = c->stream;
+            SB_CHECK_CUDA(c, cudaEventRecord(c->cap_in, main_stream));
+            SB_CHECK_CUDA(c, cudaStreamWaitEvent(c->cap_stream, c->cap_in, 0));
+            c->stream = c->cap_stream;
+            st = batch_steps_graph(c, key, steps - 1);
+            c->stream = main_stream;
+            SB_CHECK_CUDA(c, cudaEventRecord(c->cap_out, c->cap_stream));
+            SB_CHECK_CUDA(c, cudaStreamWaitEvent(main_stream, c->cap_out, 0));
+        } else {
+            for (int s = 1; s < steps && st == SB_OK; s++) st = batch_step_enqueue(c);
+        }
+    }
+    c->tune[SB_TUNE_STALL_TEST] = 0;
+    SB_TRY(st);
+    if (fr_min_out)
+        SB_CHECK_CUDA(c, cudaMemcpyAsync(fr_min_out, c->bs_frmin, sizeof(int32_t) * (size_t)G, cudaMemcpyDeviceToDevice,
+                                         c->stream));
+    if (n_states_out)
+        SB_CHECK_CUDA(c, cudaMemcpyAsync(n_states_out, c->bs_ns, sizeof(int32_t) * (size_t)G, cudaMemcpyDeviceToDevice,
+                                         c->stream));
+    // the last step is the context's sampled batch (scored already)
+    c->tree_begin = tree_begin + (int64_t)(steps - 1) * K;
+    c->counts_valid = true;
+    return SB_OK;
 }
 
 extern "C" sb_status sb_frustration(sb_ctx* c, int32_t* counts_out, uint64_t* hashes_out)

@@ -331,6 +331,10 @@ __device__ __forceinline__ uint32_t cl_bit(const uint64_t* row, const uint64_t* 
 // One block per 64-vertex chunk.  For each tree of the batch: store the state
 // (trees that created a state in this batch), or compare with the state it
 // was matched to (its creator's labels, or the stored bits of an older state).
+// The chunk's 64 label rows are staged in shared memory and turned into the
+// trees' 64-vertex columns in place: a warp takes one word at a time and
+// transposes its 64 x 64 bit block with four 32 x 32 warp transposes, so
+// that slot [r][w] then holds the canonical column of tree 64 w + r.
 #define CLV_THREADS 256
 __global__ void __launch_bounds__(CLV_THREADS)
     k_cloud_verify(const uint64_t* __restrict__ lab, int64_t n, int W, const uint64_t* __restrict__ flipw, int64_t K,
@@ -346,22 +350,29 @@ __global__ void __launch_bounds__(CLV_THREADS)
         rows[i] = r < nv ? lab[(v0 + r) * W + w] : 0;
     }
     __syncthreads();
+    const unsigned lane = threadIdx.x & 31u;
+    const uint64_t valid = nv >= 64 ? ~0ull : ((1ull << nv) - 1ull);
+    for (int w = (int)(threadIdx.x >> 5); w < W; w += CLV_THREADS / 32) {
+        const uint64_t a = rows[lane * W + w], b = rows[(lane + 32) * W + w];  // vertices lane, lane + 32
+        const uint64_t lo = (uint64_t)warp_transpose32((uint32_t)a, lane) |
+                            ((uint64_t)warp_transpose32((uint32_t)b, lane) << 32);          // tree 64 w + lane
+        const uint64_t hi = (uint64_t)warp_transpose32((uint32_t)(a >> 32), lane) |
+                            ((uint64_t)warp_transpose32((uint32_t)(b >> 32), lane) << 32);  // tree 64 w + 32 + lane
+        const uint64_t f = flipw[w];
+        rows[lane * W + w] = lo ^ (((f >> lane) & 1ull) ? valid : 0ull);
+        rows[(lane + 32) * W + w] = hi ^ (((f >> (32 + lane)) & 1ull) ? valid : 0ull);
+    }
+    __syncthreads();
     for (int64_t i = threadIdx.x; i < K; i += CLV_THREADS) {
         const int32_t s = assign[i];
         if (s < 0) continue;
-        uint64_t col = 0;
-        for (int r = 0; r < nv; r++) col |= (uint64_t)cl_bit(rows + r * W, flipw, i) << r;
+        const uint64_t col = rows[(i & 63) * W + (i >> 6)];
         const int32_t creator = rep[s];
         uint64_t* slot = bits + chunk * max_states + s;
         if (creator == (int32_t)i) {
             *slot = col;
         } else {
-            uint64_t other = 0;
-            if (creator >= 0) {
-                for (int r = 0; r < nv; r++) other |= (uint64_t)cl_bit(rows + r * W, flipw, creator) << r;
-            } else {
-                other = *slot;
-            }
+            const uint64_t other = creator >= 0 ? rows[(creator & 63) * W + (creator >> 6)] : *slot;
             if (other != col) mismatch[i] = 1;
         }
     }
@@ -771,7 +782,8 @@ __device__ bool bc_same(const uint64_t* lab, int W, const uint64_t* flip, int64_
 
 __global__ void __launch_bounds__(BC_THREADS)
     k_batch_cloud(const uint64_t* __restrict__ hashes, const int32_t* __restrict__ counts, int64_t KP, int K,
-                  int64_t tree0, const uint64_t* __restrict__ lab, int W, const uint64_t* __restrict__ flipw,
+                  const int64_t* __restrict__ tree0p, const uint64_t* __restrict__ lab, int W,
+                  const uint64_t* __restrict__ flipw,
                   const int32_t* __restrict__ voff, int32_t* __restrict__ nstates_out, int32_t* __restrict__ frmin_out,
                   sb_cloud_entry* __restrict__ entries)
 {
@@ -883,7 +895,7 @@ __global__ void __launch_bounds__(BC_THREADS)
                 e.hash = hashes[g * KP + t];
                 e.S = counts[g * KP + t];
                 e.count = cnt[t];
-                e.first_tree = tree0 + t;
+                e.first_tree = *tree0p + t;
                 entries[g * (int64_t)K + rank[t]] = e;
             }
     if (tid == 0) {
@@ -909,8 +921,8 @@ extern "C" sb_status sb_batch_cloud(sb_ctx* c, int32_t* n_states_out, int32_t* f
     if (st == SB_OK) {
         SbProf prof(c, SB_PROF_CLOUD);
         k_batch_cloud<<<(unsigned)G, BC_THREADS, 0, c->stream>>>(c->hashes, c->counts, 64 * (int64_t)c->W, (int)c->K,
-                                                                c->tree_begin, c->labels, c->W, c->flipw, c->b_voff,
-                                                                ns, fm, ent);
+                                                                sb_tree0_ptr(c->sync), c->labels, c->W, c->flipw,
+                                                                c->b_voff, ns, fm, ent);
         st = sb_after_launch(c, "k_batch_cloud");
     }
     if (st == SB_OK) st = sb_copy_out(c, n_states_out, ns, sizeof(int32_t) * (size_t)G);
@@ -921,4 +933,16 @@ extern "C" sb_status sb_batch_cloud(sb_ctx* c, int32_t* n_states_out, int32_t* f
     sb_dfree(c, fm);
     sb_dfree(c, ent);
     return st;
+}
+
+// per-graph clouds of the current batch's trees into device arrays (no
+// entries, no host synchronisation): the cloud step of sb_batch_steps
+sb_status sb_batch_cloud_enqueue(sb_ctx* c, int32_t* n_states, int32_t* fr_min)
+{
+    SbProf prof(c, SB_PROF_CLOUD);
+    k_batch_cloud<<<(unsigned)c->batch_G, BC_THREADS, 0, c->stream>>>(c->hashes, c->counts, 64 * (int64_t)c->W,
+                                                                     (int)c->K, sb_tree0_ptr(c->sync), c->labels,
+                                                                     c->W, c->flipw, c->b_voff, n_states, fr_min,
+                                                                     nullptr);
+    return sb_after_launch(c, "k_batch_cloud");
 }

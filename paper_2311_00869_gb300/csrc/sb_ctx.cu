@@ -185,9 +185,15 @@ sb_status sb_copy_out(sb_ctx* c, void* dst, const void* src_dev, size_t bytes)
 void sb_release_batch(sb_ctx* c)
 {
     SB_FREE(labels);
+    c->labels_cap = 0;
     SB_FREE(flipw);
+    c->flipw_cap = 0;
     SB_FREE(hashes);
+    c->hashes_cap = 0;
+    SB_FREE(hwsum);
+    c->hwsum_cap = 0;
     SB_FREE(counts);
+    c->counts_cap = 0;
     SB_FREE(vis);
     SB_FREE(fr0);
     SB_FREE(fr1);
@@ -255,6 +261,14 @@ void sb_release_graph(sb_ctx* c)
     if (c->gl_exec) cudaGraphExecDestroy(c->gl_exec);
     c->gl_exec = nullptr;
     memset(c->gl_exec_key, 0, sizeof(c->gl_exec_key));
+    SB_FREE(bs_frmin);
+    SB_FREE(bs_fm);
+    SB_FREE(bs_ns);
+    c->bs_cap = 0;
+    if (c->bs_exec) cudaGraphExecDestroy(c->bs_exec);
+    c->bs_exec = nullptr;
+    memset(c->bs_exec_key, 0, sizeof(c->bs_exec_key));
+    c->graph_gen++;
     SB_FREE(b_voff);
     SB_FREE(b_eoff);
     SB_FREE(vgid);
@@ -331,8 +345,8 @@ extern "C" sb_status sb_set_tuning(sb_ctx* c, int32_t knob, int64_t value)
     if (!c || knob < 0 || knob >= SB_TUNE_N || value < 0) return SB_ERR_ARG;
     if (knob == SB_TUNE_BFS_WORDS && value > SB_WORDS_MAX) return sb_fail(c, SB_ERR_ARG, "at most 32 words per launch");
     if (knob == SB_TUNE_SCORE_BLOCKS_SM && value > 32) return sb_fail(c, SB_ERR_ARG, "at most 32 blocks per SM");
-    if (knob == SB_TUNE_GL_LANES && value != 0 && value != 8 && value != 32)
-        return sb_fail(c, SB_ERR_ARG, "graphL lanes must be 8 or 32");
+    if (knob == SB_TUNE_GL_LANES && value != 0 && value != 8 && value != 16 && value != 32)
+        return sb_fail(c, SB_ERR_ARG, "graphL lanes must be 8, 16 or 32");
     if (knob == SB_TUNE_BFS_GROUP && (value > 32 || (value & (value - 1)) != 0))
         return sb_fail(c, SB_ERR_ARG, "BFS group must be a power of two <= 32");
     if (knob == SB_TUNE_WAIT_US && value > 60000000) return sb_fail(c, SB_ERR_ARG, "wait limit at most 6e7 us");
@@ -357,8 +371,19 @@ extern "C" sb_status sb_get_tuning(sb_ctx* c, int32_t knob, int64_t* value)
 extern "C" sb_status sb_sync(sb_ctx* c)
 {
     if (!c) return SB_ERR_ARG;
+    SB_CHECK_CUDA(c, cudaSetDevice(c->device));
     SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
     SB_CHECK_CUDA(c, cudaGetLastError());
+    if (c->sync) {
+        // errors that sb_batch_steps left on the device
+        uint32_t sticky = 0;
+        SB_CHECK_CUDA(c, cudaMemcpy(&sticky, c->sync + 34, sizeof(sticky), cudaMemcpyDeviceToHost));
+        if (sticky) {
+            SB_CHECK_CUDA(c, cudaMemset(c->sync + 34, 0, sizeof(uint32_t)));
+            if (sticky & 1u) return sb_fail(c, SB_ERR_TIMEOUT, "a bounded device wait gave up during the steps");
+            return sb_fail(c, SB_ERR_DEVICE_CHECK, "a device-side check failed during the steps");
+        }
+    }
     return SB_OK;
 }
 

@@ -470,9 +470,11 @@ template <bool STEP>
 static sb_status gl_rows_launch(sb_ctx* c, GlArgs& A)
 {
     const bool vec4 = (A.R % 4 == 0) && (((uintptr_t)A.gin & 15) == 0);
-    const bool wide = c->tune[SB_TUNE_GL_LANES] == 32;
-    const void* fn = vec4 ? (wide ? (const void*)k_gl_rows<4, 32, STEP> : (const void*)k_gl_rows<4, 8, STEP>)
-                          : (const void*)k_gl_rows<1, 32, STEP>;
+    const int64_t lanes = c->tune[SB_TUNE_GL_LANES];
+    const void* fn = !vec4        ? (const void*)k_gl_rows<1, 32, STEP>
+                     : lanes == 32 ? (const void*)k_gl_rows<4, 32, STEP>
+                     : lanes == 16 ? (const void*)k_gl_rows<4, 16, STEP>
+                                   : (const void*)k_gl_rows<4, 8, STEP>;
     size_t smem = STEP ? sizeof(uint32_t) * 2 * (size_t)A.R : 0;
     if (smem > 48 * 1024) SB_CHECK_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;

@@ -123,8 +123,13 @@ struct sb_ctx {
     int W = 0;                    // words = ceil(K / 64)
     uint64_t* labels = nullptr;   // n x W raw labels (root label 0)
     uint64_t* flipw = nullptr;    // W: label of vertex 0 per word (canonical flip)
+    size_t flipw_cap = 0;
     uint64_t* hashes = nullptr;   // K
+    size_t hashes_cap = 0;
+    uint64_t* hwsum = nullptr;    // per graph: total vertex weight (state-hash complement)
+    size_t hwsum_cap = 0;
     int32_t* counts = nullptr;    // K
+    size_t counts_cap = 0;
     bool counts_valid = false;
     bool batch_in_cloud = false;
     size_t labels_cap = 0;
@@ -136,7 +141,9 @@ struct sb_ctx {
     int32_t* done = nullptr;
     uint64_t* hubnew = nullptr;
     uint64_t* hubbest = nullptr;
-    uint32_t* sync = nullptr;     // [0..2] level counters, [4] barrier count, [5] barrier gen, [6] error
+    uint32_t* sync = nullptr;     // [0..2] level counters, [4] barrier count, [5] barrier gen, [6] error,
+                                  // [32..33] first tree of the batch (int64, read by the kernels),
+                                  // [34] sticky errors of sb_batch_steps
     size_t bfs_cap_words = 0;
 
     // Kruskal (Boruvka) scratch, [vertex][tree of the pass]
@@ -178,6 +185,16 @@ struct sb_ctx {
     size_t gl_colmax_cap = 0;
     int32_t* gl_misc = nullptr;
     size_t gl_misc_cap = 0;
+
+    // batched steps (sb_batch_steps): per-graph outputs of a step and the
+    // captured step (replayed while its key stays the same)
+    int32_t* bs_frmin = nullptr;   // G: smallest S over the steps
+    int32_t* bs_fm = nullptr;      // G: smallest S of the step
+    int32_t* bs_ns = nullptr;      // G: distinct states of the step
+    size_t bs_cap = 0;
+    cudaGraphExec_t bs_exec = nullptr;
+    uint64_t bs_exec_key[8] = {0};
+    uint64_t graph_gen = 0;        // changes with every loaded graph
 
     // captured descent loop (replayed while its arguments stay the same)
     cudaGraphExec_t gl_exec = nullptr;
@@ -254,6 +271,11 @@ sb_status sb_score_batch(sb_ctx* c);
 // once a sampler has written raw labels
 sb_status sb_batch_begin(sb_ctx* c, uint64_t seed, int64_t tree_begin, int64_t K);
 sb_status sb_batch_end(sb_ctx* c);
+// launches of one batched step with no host synchronisation (sb_batch_steps)
+sb_status sb_score_enqueue(sb_ctx* c);
+sb_status sb_batch_cloud_enqueue(sb_ctx* c, int32_t* n_states, int32_t* fr_min);
+// device copy of the batch's first tree index (read by the kernels)
+__host__ __device__ __forceinline__ int64_t* sb_tree0_ptr(uint32_t* sync) { return (int64_t*)(sync + 32); }
 
 #define SB_CHECK_CUDA(ctx, call)                                   \
     do {                                                           \
@@ -270,6 +292,28 @@ sb_status sb_batch_end(sb_ctx* c);
 __host__ __device__ __forceinline__ int64_t sb_cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 __device__ __forceinline__ unsigned sb_lane() { return threadIdx.x & 31u; }
+
+// 32 x 32 bit-matrix transpose across a warp: on entry lane k holds row k
+// (bit j = element (k, j)); on exit lane j holds column j (bit k = element
+// (k, j)).  Stage s swaps the off-diagonal s x s blocks of every 2s x 2s
+// block; after the five stages every block has been transposed.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, unsigned lane)
+{
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const uint32_t m = s == 16 ? 0x0000FFFFu : s == 8 ? 0x00FF00FFu : s == 4 ? 0x0F0F0F0Fu
+                         : s == 2 ? 0x33333333u : 0x55555555u;  // columns j with (j & s) == 0
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, s);
+        const bool upper = (lane & (unsigned)s) == 0;
+        // the upper row keeps its left columns and takes the partner's left
+        // columns into its right ones; the lower row keeps its right columns
+        // and takes the partner's right columns into its left ones
+        const uint32_t keep = upper ? m : ~m;
+        const uint32_t t = upper ? (y << s) : (y >> s);
+        x = (x & keep) | (t & ~keep);
+    }
+    return x;
+}
 
 // ---------------------------------------------------------------- TMA (bulk)
 // One-dimensional bulk copies global -> shared (cp.async.bulk) completing on

@@ -241,12 +241,13 @@ static const void* score_kernel(int G)
     }
 }
 
-// counts of the current batch (into c->counts): one launch over all W <= 64 words
-sb_status sb_score_batch(sb_ctx* c)
+// counts of the current batch (into c->counts): the launches only (no host
+// synchronisation); a tile copy that times out sets sync[28]
+sb_status sb_score_enqueue(sb_ctx* c)
 {
-    if (c->counts_valid) return SB_OK;
     const int64_t ngraphs = c->batch_G > 0 ? c->batch_G : 1;
     SB_CHECK_CUDA(c, cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 64 * c->W * ngraphs, c->stream));
+    SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync + 28, 0, sizeof(uint32_t), c->stream));
     if (c->m > 0) {
         const bool seg = c->batch_G > 0;
         const int Wb = c->W;
@@ -272,11 +273,21 @@ sb_status sb_score_batch(sb_ctx* c)
         A.err = c->sync + 28;
         A.wait = sb_wait_cycles(c);
         A.drain = std::max(A.wait, SB_WAIT_DEFAULT_US * (long long)c->clock_khz / 1000);
-        SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync + 28, 0, sizeof(uint32_t), c->stream));
         void* args[] = {&A};
         SbProf prof(c, SB_PROF_SCORE);
         SB_CHECK_CUDA(c, cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(SC_THREADS), args, smem, c->stream));
-        SB_TRY(sb_after_launch(c, "k_score"));
+        return sb_after_launch(c, "k_score");
+    }
+    return SB_OK;
+}
+
+// counts of the current batch, checked: waits for the launches and reports a
+// tile copy that timed out
+sb_status sb_score_batch(sb_ctx* c)
+{
+    if (c->counts_valid) return SB_OK;
+    SB_TRY(sb_score_enqueue(c));
+    if (c->m > 0) {
         uint32_t err = 0;
         SB_CHECK_CUDA(c, cudaMemcpyAsync(&err, c->sync + 28, sizeof(err), cudaMemcpyDeviceToHost, c->stream));
         SB_CHECK_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -285,4 +296,3 @@ sb_status sb_score_batch(sb_ctx* c)
     c->counts_valid = true;
     return SB_OK;
 }
-

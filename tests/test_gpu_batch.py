@@ -148,3 +148,57 @@ def test_batch_of_64_benchmark_graphs_matches_per_graph_oracle():
         assert np.array_equal(e["count"], rcl["count"]), g
         assert np.array_equal(e["S"], rcl["S"]), g
         assert np.array_equal(e["hash"], rcl["H"]), g
+
+
+def test_batch_steps_captured_equal_uncaptured_and_oracle():
+    """sb_batch_steps runs several graphBpp steps over a batch with no host
+    synchronisation; with use_graph the step is captured into a CUDA graph
+    and replayed (the device moves the tree range on).  Both forms give, per
+    graph, the oracle's smallest S over all the steps' trees and the
+    oracle's number of distinct states in the last step; the last step's
+    counts and hashes are the context's batch.  A second call reuses the
+    captured graph from another first tree.  A stalled barrier during the
+    steps is reported by sync() as SB_ERR_TIMEOUT."""
+    import torch
+
+    import paper_2311_00869_gb300 as P
+
+    graphs = _graphs(21, seed=9)
+    sb = P.SignedBal(0)
+    try:
+        nv, mv = sb.load_batch(graphs)
+        refs = [O.clean_graph(*g) for g in graphs]
+        K, steps = 64, 4
+        first = None
+        for t0 in (100, 1000):
+            out = {}
+            for use_graph in (True, False):
+                fr, ns = sb.batch_steps(3, t0, K, steps, use_graph=use_graph)
+                sb.sync()
+                counts, hashes = sb.batch_frustration()
+                out[use_graph] = (fr.cpu().numpy(), ns.cpu().numpy(), counts.cpu().numpy(),
+                                  hashes.cpu().numpy().view(np.uint64))
+            for a, b in zip(out[True], out[False]):
+                assert np.array_equal(a, b)
+            fr, ns, counts, hashes = out[True]
+            first = fr if first is None else first
+            for g, r in enumerate(refs):
+                ref = O.sample(r, 3, t0, K * steps)
+                assert fr[g] == ref["counts"].min(), g
+                last = slice((steps - 1) * K, steps * K)
+                assert np.array_equal(counts[g], ref["counts"][last]), g
+                assert np.array_equal(hashes[g], ref["hashes"][last]), g
+                rc = O.cloud(ref["labels"][last], ref["counts"][last], t0=t0 + (steps - 1) * K)
+                assert ns[g] == rc["S"].shape[0], g
+        # a stalled barrier in the steps comes back from sync(), and the context recovers
+        sb.set_tuning(wait_us=20000, stall_test=1)
+        sb.batch_steps(3, 0, K, 2, use_graph=False)
+        with pytest.raises(P.SignedBalError) as e:
+            sb.sync()
+        assert e.value.code == -12
+        sb.set_tuning(wait_us=0)
+        fr, _ = sb.batch_steps(3, 100, K, steps, use_graph=True)
+        sb.sync()
+        assert np.array_equal(fr.cpu().numpy(), first)
+    finally:
+        sb.close()

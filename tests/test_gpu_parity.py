@@ -175,6 +175,20 @@ def test_rmat_multiword_ragged(P, sb):
     assert np.array_equal(lab, ref["labels"])
 
 
+@pytest.mark.parametrize("words", [3, 8, 13, 32])
+def test_bfs_words_per_launch_agree_with_the_oracle(P, sb, words):
+    """Any number of 64-tree words per BFS launch gives the oracle's trees,
+    labels, counts and hashes, with split rows, parents and a ragged last
+    word (the words of a call split over launches of `words` words)."""
+    n, a, b, s = _hub_graph(seed=91, n=1500, extra=4000, neg=0.3)
+    g = load_both(sb, n, a, b, s)
+    assert np.diff(g.rowptr).max() > 1024  # split rows
+    sb.set_tuning(bfs_words=words)
+    check_batch(P, sb, g, seed=17 + words, t0=300, K=64 * words - 5, parents=True)
+    check_batch(P, sb, g, seed=18 + words, t0=7, K=64 * 64, parents=False)
+    sb.set_tuning(bfs_words=0)
+
+
 def test_determinism_repeat(P, sb):
     n, u, v, s = synth.rmat_two_faction(scale=12, m_target=1 << 15, seed=3)
     sb.load_graph(n, u, v, s)
@@ -323,6 +337,26 @@ def test_graphl_fwd_bwd_against_fp64(P, sb, R):
     assert np.all(np.abs(grad - ref) <= comp_bound)
     # bitwise reproducible
     assert torch.equal(sb.graphL_bwd(G, gout), sb.graphL_bwd(G, gout))
+
+
+def test_graphl_segment_widths_give_identical_gradients(P, sb):
+    """The graphL row kernel sums every row in the same fixed order whatever
+    the width of its column segments (32, 64 or 128 columns), so the
+    adjoint (Eq. 4) is bitwise the same for every lane knob, and within the
+    float32 bound of the float64 oracle."""
+    n, u, v, s = synth.rmat_two_faction(scale=11, m_target=1 << 14, seed=4)
+    g = load_both(sb, n, u, v, s)
+    R = 96
+    gam = torch.from_numpy(synth.gamma0(g.n, R, seed=6)).cuda()
+    gout = torch.from_numpy(np.random.default_rng(2).uniform(0.5, 2.0, R).astype(np.float32)).cuda()
+    grads = {}
+    for lanes in (8, 16, 32):
+        sb.set_tuning(gl_lanes=lanes)
+        grads[lanes] = sb.graphL_bwd(gam, gout).cpu().numpy()
+    sb.set_tuning(gl_lanes=0)
+    assert np.array_equal(grads[8], grads[16]) and np.array_equal(grads[8], grads[32])
+    want = O.graphl_grad_f64(g, gam.cpu().numpy().astype(np.float64), gout.cpu().numpy().astype(np.float64))
+    assert np.linalg.norm(grads[8] - want) <= 1e-5 * np.linalg.norm(want)
 
 
 def test_graphl_autograd_function(P, sb):
@@ -562,7 +596,7 @@ def test_argument_and_state_errors(P):
         with pytest.raises(P.SignedBalError) as e:
             sb.sample_trees(0, -1, 8)
         assert e.value.code == ARG
-        for knob, val in (("bfs_words", 33), ("bfs_group", 3), ("gl_lanes", 16), ("score_blocks_sm", 99),
+        for knob, val in (("bfs_words", 33), ("bfs_group", 3), ("gl_lanes", 12), ("score_blocks_sm", 99),
                           ("wait_us", 60000001), ("stall_test", 2)):
             with pytest.raises(P.SignedBalError) as e:
                 sb.set_tuning(**{knob: val})
