@@ -348,7 +348,9 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
     const int wofs = w0 + gl;
     uint16_t* queue = queues + (tid / G) * (BFS_QUEUE_PER_LANE * G);
     uint32_t n_scan = 0, n_hash = 0, n_hash_hub = 0;  // work counters
-    int L = 1;
+    // level 1 is built top-down before the launch (k_bfs_level1): every
+    // neighbour of a root has that root as its only candidate
+    int L = 2;
     while (true) {
         const uint64_t* cur = (L & 1) ? A.fr0 : A.fr1;
         uint64_t* nxt = (L & 1) ? A.fr1 : A.fr0;
@@ -549,6 +551,40 @@ __global__ void k_bfs_roots(int64_t n, int Wb, int w0, int64_t K, uint64_t S, co
     atomicOr((unsigned long long*)(vis + (int64_t)r * Wb + w), bit);
     atomicOr((unsigned long long*)(fr0 + (int64_t)r * Wb + w), bit);
     if (parents) parents[tb * n + r] = -1;
+}
+
+// BFS level 1, top-down: a neighbour v of tree t's root r joins the tree at
+// level 1 with r as its parent (the only vertex of level 0, so no hash
+// decides), label lab(r) ^ neg(r, v) = neg(r, v).  One warp per (graph,
+// tree of the launch); trees of one word may reach the same vertex, hence
+// the atomics.  Frontier of level 1 -> fr1 (read as the current frontier of
+// level 2).
+__global__ void k_bfs_level1(int64_t n, int Wb, int Wt, int w0, int64_t K, uint64_t S, const int64_t* tree0p,
+                             const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, uint64_t* vis,
+                             uint64_t* fr1, uint64_t* lab, int32_t* parents, const int32_t* voff, int64_t G)
+{
+    const int64_t per = 64 * (int64_t)Wb;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= per * G) return;
+    const int64_t g = warp / per;
+    const int64_t i = warp - g * per;         // tree within this launch
+    const int64_t tb = 64 * (int64_t)w0 + i;  // tree within the batch
+    if (tb >= K) return;
+    const uint64_t key = sb_tree_key(S, *tree0p + tb);
+    const int64_t base = voff ? voff[g] : 0;
+    const int64_t ng = voff ? voff[g + 1] - voff[g] : n;
+    const int64_t r = base + sb_root(key, ng);
+    const int w = (int)(i >> 6);
+    const unsigned long long bit = 1ull << (i & 63);
+    for (int32_t j = rowptr[r] + lane; j < rowptr[r + 1]; j += 32) {
+        const uint32_t cv = (uint32_t)col[j];
+        const int64_t v = cv & SB_ID_MASK;
+        atomicOr((unsigned long long*)(vis + v * Wb + w), bit);
+        atomicOr((unsigned long long*)(fr1 + v * Wb + w), bit);
+        if (cv >> 31) atomicOr((unsigned long long*)(lab + v * Wt + w0 + w), bit);
+        if (parents) parents[tb * n + v] = (int32_t)(r - base);
+    }
 }
 
 // canonical flip per graph and word: the raw label of the graph's vertex 0
@@ -763,6 +799,13 @@ static sb_status run_bfs(sb_ctx* c, int w0, int Wb, int32_t* parents)
     // is cleared per batch, so that an error of an earlier launch stays)
     SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync, 0, sizeof(uint32_t) * 6, c->stream));
     SB_CHECK_CUDA(c, cudaMemsetAsync(c->sync + 7, 0, sizeof(uint32_t) * 9, c->stream));
+    {
+        const int64_t warps = 64 * (int64_t)Wb * ngraphs;
+        k_bfs_level1<<<(unsigned)sb_cdiv(warps * 32, 256), 256, 0, c->stream>>>(
+            n, Wb, c->W, w0, c->K, sb_seed_key(c->seed), sb_tree0_ptr(c->sync), c->rowptr, c->col, c->vis, c->fr1,
+            c->labels, parents, c->batch_G > 0 ? c->b_voff : nullptr, ngraphs);
+        SB_TRY(sb_after_launch(c, "k_bfs_level1"));
+    }
     BfsArgs A;
     A.items = c->items;
     A.n_items = c->n_items;
