@@ -91,6 +91,14 @@ __device__ __forceinline__ unsigned group_mask(int G)
     return ((1u << G) - 1u) << base;
 }
 
+// Position of the highest set bit of a nonzero word.
+__device__ __forceinline__ int bit_high(uint32_t x)
+{
+    uint32_t r;
+    asm("bfind.u32 %0, %1;" : "=r"(r) : "r"(x));
+    return (int)r;
+}
+
 // Group-wide exclusive prefix sum over the G lanes of one vertex.
 template <int G>
 __device__ __forceinline__ int group_excl_scan(int x, unsigned gmask, int gl, int& total)
@@ -124,7 +132,8 @@ template <bool PAR, int BD, int G>
 __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint64_t* cur, const uint64_t* lab, int Wb,
                                          int Wt, int wofs, int gl, uint64_t mask, uint32_t y, uint32_t goff,
                                          const uint32_t* akey, uint32_t* best, uint8_t* labb, int32_t* bestu,
-                                         uint16_t* queue, int tid, unsigned gmask, uint64_t& once, uint32_t& nhash)
+                                         uint16_t* queue, uint32_t* hxs, int tid, unsigned gmask, uint64_t& once,
+                                         uint32_t& nhash)
 {
     for (int j = 0; j < len; j += 8) {
         uint32_t c[8];
@@ -166,22 +175,24 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
                         const uint32_t lw = (uint32_t)(l[k] >> (32 * half));
                         const int t0 = 32 * half;
                         while (m) {
-                            const int ia = __ffs(m) - 1;
-                            m &= m - 1;
-                            const int ib = m ? __ffs(m) - 1 : ia;
-                            const bool two = m != 0;
-                            m &= m - 1;
+                            // the highest and the lowest candidate (the same
+                            // one when a single candidate is left)
+                            const int ia = bit_high(m);
+                            const int ib = __ffs(m) - 1;
+                            const bool two = ia != ib;
+                            m &= ~((1u << ia) | (1u << ib));
                             const uint32_t ha = sb_fmix32(hx + ak[t0 + ia]);
                             const uint32_t hb = sb_fmix32(hx + ak[t0 + ib]);
                             const uint32_t ba = bs[t0 + ia], bb = bs[t0 + ib];
+                            // label bytes keep the winner's label in bit 0
                             if (ha <= ba) {  // <=: the minima start at 0xFFFFFFFF
                                 bs[t0 + ia] = ha;
-                                lb[t0 + ia] = (uint8_t)((lw >> ia) & 1u);
+                                lb[t0 + ia] = (uint8_t)(lw >> ia);
                                 if (PAR) bestu[BSLOT(tid, t0 + ia)] = (int32_t)u;
                             }
                             if (two && hb <= bb) {
                                 bs[t0 + ib] = hb;
-                                lb[t0 + ib] = (uint8_t)((lw >> ib) & 1u);
+                                lb[t0 + ib] = (uint8_t)(lw >> ib);
                                 if (PAR) bestu[BSLOT(tid, t0 + ib)] = (int32_t)u;
                             }
                         }
@@ -198,33 +209,29 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
                 // (two neighbours may reach the same tree) and then let the
                 // one entry equal to the minimum write its label bit
 #pragma unroll
-                for (int k = 0; k < 8; k++)
+                for (int k = 0; k < 8; k++) {
+                    // the group's table of the 8 neighbours' u ^ y (one writer per entry)
+                    if ((k & (G - 1)) == gl) hxs[k] = ((c[k] & SB_ID_MASK) - goff) ^ y;
                     for (uint64_t b = f[k]; b;) {
                         const int t = __ffsll((long long)b) - 1;
                         b &= b - 1;
                         queue[pos++] = (uint16_t)((k << 12) | (gl << 7) | (t << 1) | (int)((l[k] >> t) & 1ull));
                     }
+                }
                 __syncwarp(gmask);
                 for (int i = gl; i < T; i += G) {
                     const uint32_t e = queue[i];
                     const int k = (int)(e >> 12), ow = (int)((e >> 7) & 31u), t = (int)((e >> 1) & 63u);
-                    uint32_t ck = c[0];
-#pragma unroll
-                    for (int q = 1; q < 8; q++)
-                        if (k == q) ck = c[q];
-                    const uint32_t h = sb_fmix32((((ck & SB_ID_MASK) - goff) ^ y) + akey[KSLOT(ow, t)]);
+                    const uint32_t h = sb_fmix32(hxs[k] + akey[KSLOT(ow, t)]);
                     atomicMin(&best[BSLOT(owner0 + ow, t)], h);
                 }
                 __syncwarp(gmask);
                 for (int i = gl; i < T; i += G) {
                     const uint32_t e = queue[i];
                     const int k = (int)(e >> 12), ow = (int)((e >> 7) & 31u), t = (int)((e >> 1) & 63u);
-                    uint32_t ck = c[0];
-#pragma unroll
-                    for (int q = 1; q < 8; q++)
-                        if (k == q) ck = c[q];
-                    const uint32_t u = (ck & SB_ID_MASK) - goff;
-                    const uint32_t h = sb_fmix32((u ^ y) + akey[KSLOT(ow, t)]);
+                    const uint32_t hxk = hxs[k];
+                    const uint32_t h = sb_fmix32(hxk + akey[KSLOT(ow, t)]);
+                    const uint32_t u = hxk ^ y;
                     const int o = owner0 + ow;
                     if (best[BSLOT(o, t)] == h) {  // fmix32 is injective in u: one entry matches
                         labb[LSLOT(o, t)] = (uint8_t)(e & 1u);
@@ -312,7 +319,7 @@ __device__ __forceinline__ uint64_t winner_labels(const uint8_t* labb, int tid, 
     for (uint64_t b = mask; b;) {
         const int t = __ffsll((long long)b) - 1;
         b &= b - 1;
-        lx |= (uint64_t)labb[LSLOT(tid, t)] << t;
+        lx |= (uint64_t)(labb[LSLOT(tid, t)] & 1u) << t;
     }
     return lx;
 }
@@ -328,6 +335,7 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
     uint8_t* labb = (uint8_t*)(best + 65 * BD);   // winners' label bits, LSLOT(thread, tree)
     uint16_t* queues = (uint16_t*)(labb + 68 * BD);  // BFS_QUEUE_PER_LANE x G entries per group
     int32_t* bestu = (int32_t*)(queues + BFS_QUEUE_PER_LANE * BD);  // winners, BSLOT (PAR only)
+    uint32_t* hx_tab = (uint32_t*)(bestu + (PAR ? 65 * BD : 0));    // 8 neighbours' u ^ y per group
     __shared__ uint32_t s_any, s_stop;
 
     const int tid = threadIdx.x;
@@ -347,6 +355,7 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
     const int Wb = A.Wb, Wt = A.Wt, w0 = A.w0;
     const int wofs = w0 + gl;
     uint16_t* queue = queues + (tid / G) * (BFS_QUEUE_PER_LANE * G);
+    uint32_t* hxs = hx_tab + (tid / G) * 8;
     uint32_t n_scan = 0, n_hash = 0, n_hash_hub = 0;  // work counters
     // level 1 is built top-down before the launch (k_bfs_level1): every
     // neighbour of a root has that root as its only candidate
@@ -386,7 +395,7 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
                     // candidates cost more than the few hashes it saved)
                     best_reset<BD>(best, tid, U);
                     scan_row<PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, goff, akey, best, labb, bestu,
-                                         queue, tid, gmask, once, hub ? n_hash_hub : n_hash);
+                                         queue, hxs, tid, gmask, once, hub ? n_hash_hub : n_hash);
                     labx = winner_labels<BD>(labb, tid, once);
                 }
                 if (hub) {
@@ -775,7 +784,7 @@ static sb_status run_bfs(sb_ctx* c, int w0, int Wb, int32_t* parents)
     const int BD = par ? BFS_THREADS_PAR : BFS_THREADS;
     const void* fn = par ? bfs_kernel<true>(G) : bfs_kernel<false>(G);
     size_t smem = sizeof(uint32_t) * ((size_t)Wb * 65 + 65 * BD) + 68 * BD + sizeof(uint16_t) * BFS_QUEUE_PER_LANE * BD +
-                  (par ? sizeof(int32_t) * 65 * BD : 0);
+                  (par ? sizeof(int32_t) * 65 * BD : 0) + sizeof(uint32_t) * 8 * (BD / G);
     SB_CHECK_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     SB_CHECK_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BD, smem));
