@@ -91,6 +91,9 @@ __device__ __forceinline__ unsigned group_mask(int G)
     return ((1u << G) - 1u) << base;
 }
 
+// Fetch the 128-byte line at p into L2 (no register result, nothing waits).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // Position of the highest set bit of a nonzero word.
 __device__ __forceinline__ int bit_high(uint32_t x)
 {
@@ -135,11 +138,21 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
                                          uint16_t* queue, uint32_t* hxs, int tid, unsigned gmask, uint64_t& once,
                                          uint32_t& nhash)
 {
+    // frontier rows are Wb words (128 B at 16 words) at 8 Wb-byte offsets; the
+    // rows of the tile after next are fetched into L2 while this tile is
+    // hashed, one line per lane (lanes 0-7: first lines of the 8 rows, lanes
+    // 8-15: second lines)
+    const int pf_k = gl & 7, pf_line = gl >> 3;
+    const bool pf = gl < 16 && pf_line * 16 < Wb;
     for (int j = 0; j < len; j += 8) {
         uint32_t c[8];
         uint64_t f[8], l[8];
 #pragma unroll
         for (int k = 0; k < 8; k++) c[k] = (j + k < len) ? (uint32_t)__ldg(cp + j + k) : 0u;
+        if (pf && j + 16 + pf_k < len) {
+            const uint32_t cn = (uint32_t)__ldg(cp + j + 16 + pf_k);
+            prefetch_l2(cur + (int64_t)(cn & SB_ID_MASK) * Wb + 16 * pf_line);
+        }
 #pragma unroll
         for (int k = 0; k < 8; k++)
             f[k] = (j + k < len && mask) ? (cur[(int64_t)(c[k] & SB_ID_MASK) * Wb + gl] & mask) : 0ull;
