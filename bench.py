@@ -71,7 +71,9 @@ def parse():
     ap.add_argument("--gl-steps", type=int, default=500, help="graphL descent steps (--leg graphl)")
     ap.add_argument("--graphs", type=int, default=4096, help="graphs in the uneven batch (--leg batch)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default tuning knobs")
-    ap.add_argument("--gl-lanes", type=int, default=0, help="graphL lanes per row segment (8 or 32; with --no-tune)")
+    ap.add_argument("--gl-lanes", type=int, default=0, help="graphL lanes per row segment (8, 16 or 32; with --no-tune)")
+    ap.add_argument("--bfs-words", type=int, default=0, help="64-tree words per BFS launch (with --no-tune)")
+    ap.add_argument("--bfs-group", type=int, default=0, help="lanes per BFS vertex group (with --no-tune)")
     args = ap.parse_args()
     if args.leg in ("graphl", "quality", "kruskal") and args.workload == "rmat24" and args.scale is None:
         args.workload = "rmat20"  # these legs run on the 2^20 two-faction graph
@@ -360,6 +362,10 @@ def main():
         return 0
     K = args.K
     tuned = {"default": True}
+    if args.no_tune and (args.bfs_words or args.bfs_group):
+        knobs = {k: v for k, v in (("bfs_words", args.bfs_words), ("bfs_group", args.bfs_group)) if v}
+        sb.set_tuning(**knobs)
+        tuned = dict(knobs, default=False)
     if not args.no_tune:
         try:
             from paper_2311_00869_gb300 import autotune
@@ -394,7 +400,7 @@ def main():
         "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": config_dict(args, n1, m1, world),
         "gpu_launches": launches, "clocks": r["clk"], "stages_ms_per_step": stages(prof, args.steps),
     }
-    line["roofline"] = roofline(prof, n1, m1, K, r["stats"], peak_hps)
+    line["roofline"] = roofline(prof, n1, m1, K, r["stats"], peak_hps, workload_name(args), bfs_shape(sb))
     extras["roofline_score"] = roofline_family("score", prof, n1, m1, K)
     extras["roofline_hash"] = roofline_family("hash", prof, n1, m1, K)
     if not args.no_extras and rank == 0:
@@ -443,7 +449,8 @@ def side_legs(P, args, stream, peak_hps, K=1024, steps=10, warmup=3):
         out = {"n": n1, "m": m1, "trees_per_step": K, "steps": steps, "ms_per_step": r["ms_step"],
                "edge_evals_per_s": K * m1 / (r["ms_step"] / 1000.0), "trees_per_s": K / (r["ms_step"] / 1000.0),
                "stages_ms_per_step": stages(r["prof"], steps), "bfs_stats": r["stats"], "tuning": tuned,
-               "roofline": roofline_family("bfs", r["prof"], n1, m1, K, r["stats"], peak_hps),
+               "roofline": roofline_family("bfs", r["prof"], n1, m1, K, r["stats"], peak_hps,
+                                           traffic_bytes("bfs", WORKLOAD_NAMES["rmat20"], bfs_shape(sb))),
                "roofline_score": roofline_family("score", r["prof"], n1, m1, K),
                "fr_min": int(r["fr_min"])}
         out["plain_vs_batched"] = plain_leg(sb, m1)
@@ -470,25 +477,36 @@ def _src_digest(paths):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a
 # kernel, from an ncu capture of this bench's own workload (the command is in
-# the matching summary under profiles/).  A figure is reported only while the
-# kernel sources still match the digest taken when it was captured.
+# the matching summary under profiles/), keyed by (family, workload, 64-tree
+# words per BFS launch, lanes per BFS vertex group).  A figure is reported
+# only for the launch shape it was taken on, and only while the kernel
+# sources still match the digest taken when it was captured.
 _BPP_SRC = ("paper_2311_00869_gb300/csrc/sb_bpp.cu", "paper_2311_00869_gb300/csrc/sb_internal.cuh")
-NCU_TRAFFIC = {
-    "bfs": (3531305216 + 1342316288, _BPP_SRC, "6c4d6c063cf4b1545500acebecd4ca1d2d8ff8ca7bef70d0c656dc40ed4bc53e"),
-}
+NCU_TRAFFIC = {}
 
 
-def _traffic_bytes():
-    out = {}
-    for fam, (nbytes, srcs, digest) in NCU_TRAFFIC.items():
-        try:
-            out[fam] = nbytes if _src_digest(srcs) == digest else None
-        except OSError:
-            out[fam] = None
-    return out
+def bfs_shape(sb):
+    """(words per BFS launch, lanes per vertex group) the library will use."""
+    t = sb.get_tuning()
+    words = t["bfs_words"] or 32
+    gw = 1
+    while gw < words:
+        gw <<= 1
+    g = t["bfs_group"]
+    return words, (g if gw < g <= 2 * gw else gw)
 
 
-NCU_TRAFFIC_BYTES = _traffic_bytes()
+def traffic_bytes(fam, workload, shape):
+    e = NCU_TRAFFIC.get((fam, workload) + tuple(shape))
+    if e is None:
+        return None
+    nbytes, srcs, digest = e
+    try:
+        return nbytes if _src_digest(srcs) == digest else None
+    except OSError:
+        return None
+
+
 OPS_PER_HASH = 10  # per hashed candidate: + tree salt (1), the 32-bit finaliser (8), running minimum (1)
 
 
@@ -512,7 +530,7 @@ def _derived_alu_peak():
     return sms * 128 * mhz * 1e6 / 1e9, f"derived: {sms} SMs x 128 INT32 lanes x {mhz:.0f} MHz"
 
 
-def roofline_family(fam, prof, n, m, K, stats=None, peak_hps=None):
+def roofline_family(fam, prof, n, m, K, stats=None, peak_hps=None, traffic=None):
     """Roofline of one kernel family: HBM-bound families against the measured
     copy bandwidth with their algorithmic bytes per launch; the BFS against
     the measured rate of its own hash mix (sb_hash_peak: the add, finaliser
@@ -539,7 +557,7 @@ def roofline_family(fam, prof, n, m, K, stats=None, peak_hps=None):
         else:
             peak, psrc = derived, dsrc
         return {"bound": "alu", "kernel": "k_bfs", "achieved": achieved, "peak": peak, "peak_source": psrc,
-                "unit": "Gop/s", "frac": achieved / peak, "traffic": NCU_TRAFFIC_BYTES.get("bfs"),
+                "unit": "Gop/s", "frac": achieved / peak, "traffic": traffic,
                 "ops_per_hash": OPS_PER_HASH, "hashes_per_launch": hashes,
                 "algorithmic_ops_per_launch": OPS_PER_HASH * hashes, "avg_launch_ms": 1000 * avg_s,
                 "launches": launches, "derived_peak": derived, "derived_peak_source": dsrc}
@@ -555,14 +573,14 @@ def roofline_family(fam, prof, n, m, K, stats=None, peak_hps=None):
     achieved = per_launch / avg_s / 1e9
     return {"bound": "hbm", "kernel": {"score": "k_score", "hash": "k_state_hash_tab", "cloud": "cloud"}[fam],
             "achieved": achieved, "peak": hbm, "peak_source": src, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": NCU_TRAFFIC_BYTES.get(fam), "algorithmic_bytes_per_launch": per_launch,
+            "traffic": traffic, "algorithmic_bytes_per_launch": per_launch,
             "avg_launch_ms": 1000 * avg_s, "launches": launches}
 
 
-def roofline(prof, n, m, K, stats=None, peak_hps=None):
+def roofline(prof, n, m, K, stats=None, peak_hps=None, workload=None, shape=None):
     """Roofline object of the dominant kernel family."""
     fam = max(prof, key=lambda k: prof[k][0])
-    r = roofline_family(fam, prof, n, m, K, stats, peak_hps)
+    r = roofline_family(fam, prof, n, m, K, stats, peak_hps, traffic_bytes(fam, workload, shape or ()))
     return r if r is not None else {"bound": "hbm", "kernel": fam, "achieved": None, "peak": None, "unit": "GB/s",
                                     "frac": None, "traffic": None}
 
