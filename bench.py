@@ -482,7 +482,14 @@ def _src_digest(paths):
 # only for the launch shape it was taken on, and only while the kernel
 # sources still match the digest taken when it was captured.
 _BPP_SRC = ("paper_2311_00869_gb300/csrc/sb_bpp.cu", "paper_2311_00869_gb300/csrc/sb_internal.cuh")
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/k_bfs_rmat24_K4096.md (one-pass capture of the full workload; ncu prints GB to 10 MB)
+    ("bfs", "rmat24_3faction_K4096", 16, 16): (92_390_000_000 + 14_080_000_000, _BPP_SRC,
+                                               "b3bb6a976a790a524d024bce9ccd9e874bedb2f141d0d27c1f4d1e94ca82aab2"),
+    # profiles/k_bfs_rmat20_K1024.md (the --set full capture)
+    ("bfs", "rmat20_2faction_K1024", 16, 16): (3_079_237_000 + 1_254_273_000, _BPP_SRC,
+                                               "b3bb6a976a790a524d024bce9ccd9e874bedb2f141d0d27c1f4d1e94ca82aab2"),
+}
 
 
 def bfs_shape(sb):
