@@ -20,13 +20,13 @@
 
 #define BFS_THREADS 128
 #define BFS_THREADS_PAR 128
-#define BFS_QUEUE_PER_LANE 32  // candidate-queue entries per lane (overflow falls back to per-lane hashing)
+#define BFS_QUEUE_PER_LANE 24  // candidate-queue entries per lane (overflow falls back to per-lane hashing)
+#define BFS_BLOCKS_PER_SM 5     // the registers (at most 102) and shared memory (44 KB at 16 words) of one block
 #define SYNC_WORDS 48
 // Shared-memory slots of (owner thread o, tree t): owner-major rows padded so
 // that one owner's trees, and one tree of consecutive owners, fall in
 // different banks (the hash rounds walk one owner's trees in lockstep).
 #define BSLOT(o, t) ((o) * 65 + (t))  // 32-bit minima / winner ids
-#define LSLOT(o, t) ((o) * 68 + (t))  // winner label bytes
 #define KSLOT(w, t) ((w) * 65 + (t))  // tree salts of word w
 
 struct BfsArgs {
@@ -94,6 +94,18 @@ __device__ __forceinline__ unsigned group_mask(int G)
 // Fetch the 128-byte line at p into L2 (no register result, nothing waits).
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
+// Winner label bits: each lane keeps its trees' bits in two registers (trees
+// 0-31 and 32-63) while it hashes its own candidates; the queue paths, where
+// lanes write each other's trees, work on a copy in shared memory (two words
+// per thread) with atomic bit updates.
+__device__ __forceinline__ void lbit_put_atomic(uint32_t* lbits, int o, int t, uint32_t v)
+{
+    uint32_t* w = lbits + 2 * o + (t >> 5);
+    const uint32_t m = 1u << (t & 31);
+    if (v) atomicOr(w, m);
+    else atomicAnd(w, ~m);
+}
+
 // Position of the highest set bit of a nonzero word.
 __device__ __forceinline__ int bit_high(uint32_t x)
 {
@@ -120,7 +132,7 @@ __device__ __forceinline__ int group_excl_scan(int x, unsigned gmask, int gl, in
 // w0 + gl.  Neighbours are read 8 at a time so that 8 frontier gathers are in
 // flight per lane.  It keeps the running argmin of the hashed parent key over
 // the candidates in `mask`: best (initialised to 0xFFFFFFFF) holds the
-// smallest hash, labb / bestu the winner's label bit / id; keys are distinct
+// smallest hash, lbv / bestu the winner's label bit / id; keys are distinct
 // (the hash is a bijection in u), so `h <= best` accepts exactly the minimum.
 // `once` returns the trees that had a candidate.  For each tile of 8
 // neighbours the lanes hash their own candidates when their shares are even;
@@ -134,9 +146,9 @@ __device__ __forceinline__ int group_excl_scan(int x, unsigned gmask, int gl, in
 template <bool PAR, int BD, int G>
 __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint64_t* cur, const uint64_t* lab, int Wb,
                                          int Wt, int wofs, int gl, uint64_t mask, uint32_t y, uint32_t goff,
-                                         const uint32_t* akey, uint32_t* best, uint8_t* labb, int32_t* bestu,
-                                         uint16_t* queue, uint32_t* hxs, int tid, unsigned gmask, uint64_t& once,
-                                         uint32_t& nhash)
+                                         const uint32_t* akey, uint32_t* best, uint32_t* lbits, uint32_t (&lbv)[2],
+                                         int32_t* bestu, uint16_t* queue, uint32_t* hxs, int tid, unsigned gmask,
+                                         uint64_t& once, uint32_t& nhash)
 {
     // frontier rows are Wb words (128 B at 16 words) at 8 Wb-byte offsets; the
     // rows of the tile after next are fetched into L2 while this tile is
@@ -177,7 +189,6 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
                 // with no queue and no synchronisation
                 const uint32_t* ak = akey + KSLOT(gl, 0);
                 uint32_t* bs = best + BSLOT(tid, 0);
-                uint8_t* lb = labb + LSLOT(tid, 0);
 #pragma unroll
                 for (int k = 0; k < 8; k++) {
                     const uint32_t u = (c[k] & SB_ID_MASK) - goff;
@@ -197,15 +208,15 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
                             const uint32_t ha = sb_fmix32(hx + ak[t0 + ia]);
                             const uint32_t hb = sb_fmix32(hx + ak[t0 + ib]);
                             const uint32_t ba = bs[t0 + ia], bb = bs[t0 + ib];
-                            // label bytes keep the winner's label in bit 0
+                            // the winner's label bit goes into bit t of the half's label word
                             if (ha <= ba) {  // <=: the minima start at 0xFFFFFFFF
                                 bs[t0 + ia] = ha;
-                                lb[t0 + ia] = (uint8_t)(lw >> ia);
+                                lbv[half] ^= (lbv[half] ^ lw) & (1u << ia);
                                 if (PAR) bestu[BSLOT(tid, t0 + ia)] = (int32_t)u;
                             }
                             if (two && hb <= bb) {
                                 bs[t0 + ib] = hb;
-                                lb[t0 + ib] = (uint8_t)(lw >> ib);
+                                lbv[half] ^= (lbv[half] ^ lw) & (1u << ib);
                                 if (PAR) bestu[BSLOT(tid, t0 + ib)] = (int32_t)u;
                             }
                         }
@@ -213,6 +224,9 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
                 }
                 continue;
             }
+            // the queue paths update other lanes' label bits: through shared memory
+            lbits[2 * tid] = lbv[0];
+            lbits[2 * tid + 1] = lbv[1];
             int T;
             int pos = group_excl_scan<G>(cnt, gmask, gl, T);
             if (T <= BFS_QUEUE_PER_LANE * G) {
@@ -247,11 +261,13 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
                     const uint32_t u = hxk ^ y;
                     const int o = owner0 + ow;
                     if (best[BSLOT(o, t)] == h) {  // fmix32 is injective in u: one entry matches
-                        labb[LSLOT(o, t)] = (uint8_t)(e & 1u);
+                        lbit_put_atomic(lbits, o, t, e & 1u);
                         if (PAR) bestu[BSLOT(o, t)] = (int32_t)u;
                     }
                 }
                 __syncwarp(gmask);
+                lbv[0] = lbits[2 * tid];
+                lbv[1] = lbits[2 * tid + 1];
                 continue;
             }
             // many candidates: one neighbour at a time
@@ -272,7 +288,7 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
                         const uint32_t h = sb_fmix32(hx + akey[KSLOT(gl, t)]);
                         if (h <= best[BSLOT(tid, t)]) {  // <=: the minima start at 0xFFFFFFFF
                             best[BSLOT(tid, t)] = h;
-                            labb[LSLOT(tid, t)] = (uint8_t)((l[k] >> t) & 1ull);
+                            lbit_put_atomic(lbits, tid, t, (uint32_t)(l[k] >> t) & 1u);
                             if (PAR) bestu[BSLOT(tid, t)] = (int32_t)u;
                         }
                     }
@@ -298,23 +314,24 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
                     const uint32_t ba = best[BSLOT(oa, ta)], bb = best[BSLOT(ob, tb)];
                     if (ha <= ba) {
                         best[BSLOT(oa, ta)] = ha;
-                        labb[LSLOT(oa, ta)] = (uint8_t)(ea & 1u);
+                        lbit_put_atomic(lbits, oa, ta, ea & 1u);
                         if (PAR) bestu[BSLOT(oa, ta)] = (int32_t)u;
                     }
                     if (two && hb <= bb) {
                         best[BSLOT(ob, tb)] = hb;
-                        labb[LSLOT(ob, tb)] = (uint8_t)(eb & 1u);
+                        lbit_put_atomic(lbits, ob, tb, eb & 1u);
                         if (PAR) bestu[BSLOT(ob, tb)] = (int32_t)u;
                     }
                 }
                 __syncwarp(gmask);
             }
+            lbv[0] = lbits[2 * tid];
+            lbv[1] = lbits[2 * tid + 1];
         }
     }
 }
 
-// Resets the running minima of the trees in `mask` and, after a hash pass,
-// collects the winners' label bits.
+// Resets the running minima of the trees in `mask`.
 template <int BD>
 __device__ __forceinline__ void best_reset(uint32_t* best, int tid, uint64_t mask)
 {
@@ -325,28 +342,16 @@ __device__ __forceinline__ void best_reset(uint32_t* best, int tid, uint64_t mas
     }
 }
 
-template <int BD>
-__device__ __forceinline__ uint64_t winner_labels(const uint8_t* labb, int tid, uint64_t mask)
-{
-    uint64_t lx = 0;
-    for (uint64_t b = mask; b;) {
-        const int t = __ffsll((long long)b) - 1;
-        b &= b - 1;
-        lx |= (uint64_t)(labb[LSLOT(tid, t)] & 1u) << t;
-    }
-    return lx;
-}
-
 template <int G, bool PAR>
-__global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
+__global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, PAR ? 2 : BFS_BLOCKS_PER_SM)
     k_bfs(BfsArgs A)
 {
     constexpr int BD = PAR ? BFS_THREADS_PAR : BFS_THREADS;
     extern __shared__ uint32_t smem[];
     uint32_t* akey = smem;                        // tree salts, KSLOT(word, tree)
     uint32_t* best = smem + A.Wb * 65;            // running minima, BSLOT(thread, tree)
-    uint8_t* labb = (uint8_t*)(best + 65 * BD);   // winners' label bits, LSLOT(thread, tree)
-    uint16_t* queues = (uint16_t*)(labb + 68 * BD);  // BFS_QUEUE_PER_LANE x G entries per group
+    uint32_t* lbits = best + 65 * BD;             // winners' label bits (queue paths), two words per thread
+    uint16_t* queues = (uint16_t*)(lbits + 2 * BD);  // BFS_QUEUE_PER_LANE x G entries per group
     int32_t* bestu = (int32_t*)(queues + BFS_QUEUE_PER_LANE * BD);  // winners, BSLOT (PAR only)
     uint32_t* hx_tab = (uint32_t*)(bestu + (PAR ? 65 * BD : 0));    // 8 neighbours' u ^ y per group
     __shared__ uint32_t s_any, s_stop;
@@ -407,9 +412,10 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, 4)
                     // first pass that singled out the trees with two or more
                     // candidates cost more than the few hashes it saved)
                     best_reset<BD>(best, tid, U);
-                    scan_row<PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, goff, akey, best, labb, bestu,
-                                         queue, hxs, tid, gmask, once, hub ? n_hash_hub : n_hash);
-                    labx = winner_labels<BD>(labb, tid, once);
+                    uint32_t lbv[2] = {0u, 0u};
+                    scan_row<PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, goff, akey, best, lbits, lbv,
+                                         bestu, queue, hxs, tid, gmask, once, hub ? n_hash_hub : n_hash);
+                    labx = (((uint64_t)lbv[1] << 32) | lbv[0]) & once;
                 }
                 if (hub) {
                     // chunk of a split row: publish the chunk minima, one atomic per tree
@@ -796,7 +802,7 @@ static sb_status run_bfs(sb_ctx* c, int w0, int Wb, int32_t* parents)
     const int G = (Gt > Gw && Gt <= 2 * Gw) ? Gt : Gw;  // widened at most twofold
     const int BD = par ? BFS_THREADS_PAR : BFS_THREADS;
     const void* fn = par ? bfs_kernel<true>(G) : bfs_kernel<false>(G);
-    size_t smem = sizeof(uint32_t) * ((size_t)Wb * 65 + 65 * BD) + 68 * BD + sizeof(uint16_t) * BFS_QUEUE_PER_LANE * BD +
+    size_t smem = sizeof(uint32_t) * ((size_t)Wb * 65 + 65 * BD + 2 * BD) + sizeof(uint16_t) * BFS_QUEUE_PER_LANE * BD +
                   (par ? sizeof(int32_t) * 65 * BD : 0) + sizeof(uint32_t) * 8 * (BD / G);
     SB_CHECK_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
