@@ -20,8 +20,12 @@
 
 #define BFS_THREADS 128
 #define BFS_THREADS_PAR 128
-#define BFS_QUEUE_PER_LANE 24  // candidate-queue entries per lane (overflow falls back to per-lane hashing)
-#define BFS_BLOCKS_PER_SM 5     // the registers (at most 102) and shared memory (44 KB at 16 words) of one block
+// Candidate-queue entries per lane (overflow falls back to per-lane hashing):
+// the host takes the largest count in this range that keeps the most blocks
+// resident per SM (the salts of a launch grow with its words).
+#define BFS_QUEUE_MIN 8
+#define BFS_QUEUE_MAX 32
+#define BFS_BLOCKS_PER_SM 5     // the registers of one block allow 5 per SM (at most 102 per thread)
 #define SYNC_WORDS 48
 // Shared-memory slots of (owner thread o, tree t): owner-major rows padded so
 // that one owner's trees, and one tree of consecutive owners, fall in
@@ -51,6 +55,7 @@ struct BfsArgs {
     const int32_t* vgoff;  // first vertex of each vertex's graph (batches), or null
     long long wait;        // SM cycles a barrier wait may take before it reports a timeout
     unsigned bar_extra;    // arrivals a barrier expects beyond the launch's blocks (0; 1 tests the timeout path)
+    int qcap;              // candidate-queue entries per lane
 };
 
 // ----------------------------------------------------------- grid barrier
@@ -147,7 +152,7 @@ template <bool PAR, int BD, int G>
 __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint64_t* cur, const uint64_t* lab, int Wb,
                                          int Wt, int wofs, int gl, uint64_t mask, uint32_t y, uint32_t goff,
                                          const uint32_t* akey, uint32_t* best, uint32_t* lbits, uint32_t (&lbv)[2],
-                                         int32_t* bestu, uint16_t* queue, uint32_t* hxs, int tid, unsigned gmask,
+                                         int32_t* bestu, uint16_t* queue, int qcap, uint32_t* hxs, int tid, unsigned gmask,
                                          uint64_t& once, uint32_t& nhash)
 {
     // frontier rows are Wb words (128 B at 16 words) at 8 Wb-byte offsets; the
@@ -229,7 +234,7 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
             lbits[2 * tid + 1] = lbv[1];
             int T;
             int pos = group_excl_scan<G>(cnt, gmask, gl, T);
-            if (T <= BFS_QUEUE_PER_LANE * G) {
+            if (T <= qcap * G) {
                 // the candidates of all 8 neighbours go through one queue of
                 // (neighbour, owner word, tree, label bit) entries; lanes hash
                 // them in lockstep, keep each tree's minimum with atomicMin
@@ -279,7 +284,7 @@ __device__ __forceinline__ void scan_row(const int32_t* cp, int len, const uint6
                 if (Tk == 0) continue;  // same for the whole group
                 const uint32_t u = (c[k] & SB_ID_MASK) - goff;  // id inside the graph
                 const uint32_t hx = u ^ y;
-                if (Tk > BFS_QUEUE_PER_LANE * G) {
+                if (Tk > qcap * G) {
                     // more candidates than the queue holds; each lane hashes
                     // its own bits (it alone owns their slots)
                     for (uint64_t b = f[k]; b;) {
@@ -351,8 +356,8 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, PAR ? 2 :
     uint32_t* akey = smem;                        // tree salts, KSLOT(word, tree)
     uint32_t* best = smem + A.Wb * 65;            // running minima, BSLOT(thread, tree)
     uint32_t* lbits = best + 65 * BD;             // winners' label bits (queue paths), two words per thread
-    uint16_t* queues = (uint16_t*)(lbits + 2 * BD);  // BFS_QUEUE_PER_LANE x G entries per group
-    int32_t* bestu = (int32_t*)(queues + BFS_QUEUE_PER_LANE * BD);  // winners, BSLOT (PAR only)
+    uint16_t* queues = (uint16_t*)(lbits + 2 * BD);  // A.qcap x G entries per group
+    int32_t* bestu = (int32_t*)(queues + ((A.qcap * BD + 1) & ~1));  // winners, BSLOT (PAR only)
     uint32_t* hx_tab = (uint32_t*)(bestu + (PAR ? 65 * BD : 0));    // 8 neighbours' u ^ y per group
     __shared__ uint32_t s_any, s_stop;
 
@@ -372,7 +377,7 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, PAR ? 2 :
 
     const int Wb = A.Wb, Wt = A.Wt, w0 = A.w0;
     const int wofs = w0 + gl;
-    uint16_t* queue = queues + (tid / G) * (BFS_QUEUE_PER_LANE * G);
+    uint16_t* queue = queues + (tid / G) * (A.qcap * G);
     uint32_t* hxs = hx_tab + (tid / G) * 8;
     uint32_t n_scan = 0, n_hash = 0, n_hash_hub = 0;  // work counters
     // level 1 is built top-down before the launch (k_bfs_level1): every
@@ -414,7 +419,7 @@ __global__ void __launch_bounds__(PAR ? BFS_THREADS_PAR : BFS_THREADS, PAR ? 2 :
                     best_reset<BD>(best, tid, U);
                     uint32_t lbv[2] = {0u, 0u};
                     scan_row<PAR, BD, G>(cp, len, cur, A.lab, Wb, Wt, wofs, gl, U, y, goff, akey, best, lbits, lbv,
-                                         bestu, queue, hxs, tid, gmask, once, hub ? n_hash_hub : n_hash);
+                                         bestu, queue, A.qcap, hxs, tid, gmask, once, hub ? n_hash_hub : n_hash);
                     labx = (((uint64_t)lbv[1] << 32) | lbv[0]) & once;
                 }
                 if (hub) {
@@ -802,11 +807,23 @@ static sb_status run_bfs(sb_ctx* c, int w0, int Wb, int32_t* parents)
     const int G = (Gt > Gw && Gt <= 2 * Gw) ? Gt : Gw;  // widened at most twofold
     const int BD = par ? BFS_THREADS_PAR : BFS_THREADS;
     const void* fn = par ? bfs_kernel<true>(G) : bfs_kernel<false>(G);
-    size_t smem = sizeof(uint32_t) * ((size_t)Wb * 65 + 65 * BD + 2 * BD) + sizeof(uint16_t) * BFS_QUEUE_PER_LANE * BD +
-                  (par ? sizeof(int32_t) * 65 * BD : 0) + sizeof(uint32_t) * 8 * (BD / G);
-    SB_CHECK_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    SB_CHECK_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BD, smem));
+    // shared memory of a block with q queue entries per lane; the largest q that
+    // keeps the most blocks resident
+    auto smem_for = [&](int q) -> size_t {
+        return sizeof(uint32_t) * ((size_t)Wb * 65 + 65 * BD + 2 * BD) + sizeof(uint16_t) * (size_t)((q * BD + 1) & ~1) +
+               (par ? sizeof(int32_t) * 65 * BD : 0) + sizeof(uint32_t) * 8 * (BD / G);
+    };
+    SB_CHECK_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for(BFS_QUEUE_MAX)));
+    int per_sm = 0, qcap = BFS_QUEUE_MAX;
+    for (int q = BFS_QUEUE_MAX; q >= BFS_QUEUE_MIN; q--) {
+        int b = 0;
+        SB_CHECK_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, BD, smem_for(q)));
+        if (b > per_sm) {
+            per_sm = b;
+            qcap = q;
+        }
+    }
+    const size_t smem = smem_for(qcap);
     if (per_sm < 1) return sb_fail(c, SB_ERR_CUDA, "BFS kernel does not fit on an SM");
     unsigned nblocks = (unsigned)(per_sm * c->num_sms);
     const int64_t n = c->n;
@@ -858,6 +875,7 @@ static sb_status run_bfs(sb_ctx* c, int w0, int Wb, int32_t* parents)
     A.vgoff = c->batch_G > 0 ? c->vgoff : nullptr;
     A.wait = sb_wait_cycles(c);
     A.bar_extra = c->tune[SB_TUNE_STALL_TEST] ? 1u : 0u;
+    A.qcap = qcap;
     void* args[] = {&A};
     {
         // a cooperative launch (every block resident for the grid barrier),
