@@ -483,14 +483,14 @@ def _src_digest(paths):
 # sources still match the digest taken when it was captured.
 _BPP_SRC = ("paper_2311_00869_gb300/csrc/sb_bpp.cu", "paper_2311_00869_gb300/csrc/sb_internal.cuh")
 NCU_TRAFFIC = {
-    # profiles/k_bfs_rmat24_K4096.md (one-pass captures of the full workload; ncu prints GB to 10 MB)
-    ("bfs", "rmat24_3faction_K4096", 32, 32): (231_990_000_000 + 29_770_000_000, _BPP_SRC,
-                                               "d07e395608c91fdb1d23810d5a4e886ff9b5cc09be0be0c263a0263dd04ce3af"),
+    # profiles/k_bfs_rmat24_K4096.md and profiles/k_bfs_rmat20_K1024.md (one-pass captures of
+    # the benchmark workloads; ncu prints GB to 10 MB)
+    ("bfs", "rmat24_3faction_K4096", 32, 32): (233_050_000_000 + 29_910_000_000, _BPP_SRC,
+                                               "d19a2ec8d19cd60565472ba7e5162344415b710f779e88ab2453464d4156c557"),
     ("bfs", "rmat24_3faction_K4096", 16, 16): (92_790_000_000 + 14_120_000_000, _BPP_SRC,
-                                               "d07e395608c91fdb1d23810d5a4e886ff9b5cc09be0be0c263a0263dd04ce3af"),
-    # profiles/k_bfs_rmat20_K1024.md (the --set full capture)
-    ("bfs", "rmat20_2faction_K1024", 16, 16): (3_117_735_000 + 1_254_234_000, _BPP_SRC,
-                                               "d07e395608c91fdb1d23810d5a4e886ff9b5cc09be0be0c263a0263dd04ce3af"),
+                                               "d19a2ec8d19cd60565472ba7e5162344415b710f779e88ab2453464d4156c557"),
+    ("bfs", "rmat20_2faction_K1024", 16, 16): (3_120_000_000 + 1_250_000_000, _BPP_SRC,
+                                               "d19a2ec8d19cd60565472ba7e5162344415b710f779e88ab2453464d4156c557"),
 }
 
 
