@@ -123,15 +123,19 @@ sb_status sb_profile_read(sb_ctx* ctx, double* ms_out, int64_t* launches_out);
                              has, so that every barrier wait runs out (a
                              test of the timeout path; no fault, nothing is
                              left running).  Reset to 0 by that call.
-   Results never depend on the first four.  sb_get_tuning returns the
-   current value. */
+   SB_TUNE_MST_WORDS         64-tree words per pass of the Kruskal sampler,
+                             1 .. 64 (0 = as many as its scratch budget of
+                             32 GiB, at most half the free memory, holds)
+   Results never depend on the first four, nor on SB_TUNE_MST_WORDS.
+   sb_get_tuning returns the current value. */
 #define SB_TUNE_BFS_WORDS 0
 #define SB_TUNE_SCORE_BLOCKS_SM 1
 #define SB_TUNE_GL_LANES 2
 #define SB_TUNE_BFS_GROUP 3
 #define SB_TUNE_WAIT_US 4
 #define SB_TUNE_STALL_TEST 5
-#define SB_TUNE_N 6
+#define SB_TUNE_MST_WORDS 6
+#define SB_TUNE_N 7
 sb_status sb_set_tuning(sb_ctx* ctx, int32_t knob, int64_t value);
 sb_status sb_get_tuning(sb_ctx* ctx, int32_t knob, int64_t* value);
 

@@ -300,7 +300,7 @@ class SignedBal:
         self._check(self.lib.sb_sync(self.h))
 
     TUNE_KNOBS = {"bfs_words": 0, "score_blocks_sm": 1, "gl_lanes": 2, "bfs_group": 3, "wait_us": 4,
-                  "stall_test": 5}
+                  "stall_test": 5, "mst_words": 6}
 
     def set_tuning(self, **knobs):
         for k, v in knobs.items():

@@ -351,6 +351,8 @@ extern "C" sb_status sb_set_tuning(sb_ctx* c, int32_t knob, int64_t value)
         return sb_fail(c, SB_ERR_ARG, "BFS group must be a power of two <= 32");
     if (knob == SB_TUNE_WAIT_US && value > 60000000) return sb_fail(c, SB_ERR_ARG, "wait limit at most 6e7 us");
     if (knob == SB_TUNE_STALL_TEST && value > 1) return sb_fail(c, SB_ERR_ARG, "stall test is 0 or 1");
+    if (knob == SB_TUNE_MST_WORDS && value > SB_TREES_MAX / 64)
+        return sb_fail(c, SB_ERR_ARG, "at most %d Kruskal words per pass", SB_TREES_MAX / 64);
     c->tune[knob] = value;
     return SB_OK;
 }

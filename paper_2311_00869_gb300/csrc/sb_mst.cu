@@ -32,7 +32,7 @@
 #define SB_MST_DEAD 0xFFFFFFFFu          // no edge leaves the component from this vertex
 #define MST_THREADS 256
 #define MST_BYTES_PER_SLOT 36            // P, R, Y (4 B each), L, B (8 B each), win (8 B)
-#define MST_PASS_BUDGET (16ull << 30)    // scratch bytes per pass of trees (at most half the free memory)
+#define MST_PASS_BUDGET (32ull << 30)    // scratch bytes per pass of trees (at most half the free memory)
 
 struct MstArgs {
     int64_t n;
@@ -260,12 +260,13 @@ extern "C" sb_status sb_sample_trees_kruskal(sb_ctx* c, uint64_t seed, int64_t t
     const int64_t n = c->n;
     const int W = c->W;
     // words per pass: as many as the scratch budget holds (at most half the
-    // free memory), at least one
+    // free memory), at least one, and at most the SB_TUNE_MST_WORDS knob
     size_t free_b = 0, total_b = 0;
     SB_CHECK_CUDA(c, cudaMemGetInfo(&free_b, &total_b));
     const uint64_t budget = std::min<uint64_t>(MST_PASS_BUDGET, (uint64_t)free_b / 2);
     const int64_t per_word = n * 64 * MST_BYTES_PER_SLOT;
     int Wp = (int)std::max<int64_t>(1, std::min<int64_t>(W, (int64_t)(budget / (uint64_t)per_word)));
+    if (c->tune[SB_TUNE_MST_WORDS] > 0) Wp = std::min<int>(Wp, (int)c->tune[SB_TUNE_MST_WORDS]);
     const int T = 64 * Wp;
     SB_TRY(mst_scratch(c, (size_t)n * T));
     // rounds: ceil(log2(largest graph)) + 1

@@ -42,6 +42,27 @@ def test_kruskal_small_graphs_match_oracle(P, K):
         sb.close()
 
 
+def test_kruskal_passes_give_identical_trees(P):
+    """Trees are grown a pass of words at a time; one word per pass (four
+    passes of 64 trees) gives the same trees, labels, counts and hashes as a
+    single pass, equal to the oracle's."""
+    sb = P.SignedBal(0)
+    try:
+        n, u, v, s = synth.random_connected(300, 900, seed=77)
+        g = O.clean_graph(n, u, v, s)
+        sb.load_graph(n, u, v, s)
+        sb.set_tuning(mst_words=1)
+        _check(P, sb, g, seed=3, t0=11, K=256)
+        one = (sb.label().clone(), [x.clone() for x in sb.frustration()])
+        sb.set_tuning(mst_words=0)
+        sb.sample_trees_kruskal(3, 11, 256)
+        assert np.array_equal(sb.label().cpu().numpy(), one[0].cpu().numpy())
+        for a, b in zip(sb.frustration(), one[1]):
+            assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+    finally:
+        sb.close()
+
+
 def test_kruskal_config1_cloud_matches_oracle(P):
     """The 1,000-vertex, 5,000-edge Erdos-Renyi graph with 64 trees: the
     cloud built from Kruskal trees equals the oracle's cloud of those trees."""

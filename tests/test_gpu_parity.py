@@ -596,7 +596,7 @@ def test_argument_and_state_errors(P):
         with pytest.raises(P.SignedBalError) as e:
             sb.sample_trees(0, -1, 8)
         assert e.value.code == ARG
-        for knob, val in (("bfs_words", 33), ("bfs_group", 3), ("gl_lanes", 12), ("score_blocks_sm", 99),
+        for knob, val in (("bfs_words", 33), ("bfs_group", 3), ("gl_lanes", 12), ("mst_words", 65), ("score_blocks_sm", 99),
                           ("wait_us", 60000001), ("stall_test", 2)):
             with pytest.raises(P.SignedBalError) as e:
                 sb.set_tuning(**{knob: val})
